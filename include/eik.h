@@ -1,0 +1,172 @@
+/*
+ * eik.h -- C ABI of the GB300 screened-Poisson eikonal solver.
+ *
+ * Method (Gurumoorthy et al., "A fast eikonal equation solver using the
+ * Schroedinger wave equation", arXiv 1403.1937):
+ *
+ *   The eikonal equation |grad S| = f (Sec. 1, Eq. eikonalEq) with S = U_k at
+ *   source nodes y_k (Sec. 3.2, after Eq. forcedPhiEquation) is replaced by the
+ *   linear equation  -hbar^2 Lap(phi) + f^2 phi = 0  (Sec. 4, Eq. phiEquation)
+ *   for phi = exp(-S/hbar), discretised with the 5-point (2D) / 7-point (3D)
+ *   finite-difference Laplacian (Sec. 6, Eq. sparse-system), and S is
+ *   recovered as S = -hbar log(phi) (Sec. 4, Eq. SfromPhi).
+ *
+ *   Discrete system solved here, for every non-source node i of a vertex-
+ *   centred grid with spacing h (nodes on the outer faces), c = hbar^2/h^2:
+ *
+ *     sum_{j~i} c*omega_ij*(phi_i - phi_j) + w_i*f_i^2*phi_i = 0,
+ *     phi_k = exp(-U_k/hbar) on the sources,
+ *
+ *   with zero flux on the outer faces in half-cell form (w_i = product over
+ *   axes b of 1/2 if i lies on a b-face; omega_ij = the same product over the
+ *   axes other than the edge's).  The matrix is a symmetric M-matrix; it is
+ *   solved matrix-free by Jacobi-preconditioned conjugate gradients.
+ *
+ * Conventions (all entry points):
+ *   - Grid arrays are dense, C order, x fastest: node (ix, iy[, iz]) is at
+ *     flat index ix + nx*(iy + ny*iz).  Values are float64.
+ *   - Pointer arguments may be device pointers or host pointers (pageable or
+ *     pinned); the library tells them apart through unified addressing.  Device
+ *     pointers must be on the device that is current at eik_create.
+ *   - Inputs are copied at eik_create / eik_set_f; the caller may free them on
+ *     return.  Output buffers are owned by the caller.
+ *   - All device work runs on an internal stream ordered after, and before,
+ *     the stream passed to eik_create: work already queued on that stream is
+ *     seen, and work queued on it after a call returns sees the results.
+ *     eik_solve and eik_grad return after the solve has finished (they must
+ *     read the convergence status).
+ *   - Errors are returned as eik_status; C++ exceptions never cross the ABI.
+ *     eik_last_error() returns a thread-local description of the last error.
+ *     After EIK_ERR_CUDA the handle should only be destroyed.
+ *   - A handle may be used by one host thread at a time.
+ */
+#ifndef EIK_H_
+#define EIK_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EIK_ABI_VERSION 1
+
+typedef struct eik_handle eik_handle;          /* opaque, library-owned */
+typedef struct CUstream_st *eik_stream_t;      /* same type as cudaStream_t */
+
+typedef enum {
+  EIK_OK = 0,
+  EIK_ERR_ARG = 1,            /* invalid argument (sizes, h, hbar, f, sources) */
+  EIK_ERR_CUDA = 2,           /* CUDA runtime error; handle unusable */
+  EIK_ERR_OOM = 3,            /* device allocation failed */
+  EIK_ERR_NOT_CONVERGED = 4,  /* max_iter reached; outputs hold the iterate */
+  EIK_ERR_BREAKDOWN = 5,      /* CG breakdown (p.Ap <= 0 or non-finite) */
+  EIK_ERR_TIMEOUT = 6,        /* a bounded device-side wait expired */
+  EIK_ERR_STATE = 7           /* call out of order (e.g. eik_grad before a solve) */
+} eik_status;
+
+enum {
+  EIK_PREC_FP64 = 0,          /* plain FP64 Jacobi-PCG */
+  EIK_PREC_MIXED = 1          /* FP32 inner CG on the rescaled system + FP64
+                                 iterative refinement (see eik_options) */
+};
+
+enum {
+  EIK_STOP_COMPONENTWISE = 0, /* max_i |r_i| / (a_ii phi_i) <= tol */
+  EIK_STOP_NORMWISE = 1       /* ||r_hat||_2 / ||b_hat||_2 <= tol (Jacobi-scaled) */
+};
+
+enum {
+  EIK_BOUNDARY_HALF_CELL = 0, /* second-order zero flux (default) */
+  EIK_BOUNDARY_DROP_EDGE = 1  /* first-order zero flux: missing edges dropped */
+};
+
+typedef struct {
+  int precision;      /* EIK_PREC_*; default EIK_PREC_FP64 */
+  double tol;         /* stopping tolerance; default 1e-12 */
+  int stop_norm;      /* EIK_STOP_*; default EIK_STOP_COMPONENTWISE */
+  int max_iter;       /* CG iterations (total over refinement steps); default
+                         200000 */
+  int boundary;       /* EIK_BOUNDARY_*; default half cell */
+  int tile_override;  /* 0 = library choice; reserved for tile selection */
+  double inner_tol;   /* mixed mode: componentwise tolerance of each FP32
+                         inner solve; 0 = library choice */
+  int max_outer;      /* mixed mode: refinement steps; 0 = library choice */
+  int reserved[7];
+} eik_options;
+
+typedef struct {
+  int outer_iters;    /* refinement steps (1 for plain FP64 without restart) */
+  int inner_iters;    /* CG iterations in total */
+  double res_cw;      /* final componentwise residual max_i |r_i|/(a_ii phi_i) */
+  double res_nw;      /* final ||r||_2 / ||b||_2 of the unscaled system */
+  double ms;          /* device time of the solve in milliseconds */
+} eik_stats;
+
+/* Fills *opt with the defaults listed above. */
+void eik_default_options(eik_options *opt);
+
+/*
+ * Creates a solver for one grid (Sec. 6, Eq. sparse-system; Sec. 3.2 sources).
+ *   ndim     2 or 3.
+ *   dims     ndim extents (nx, ny[, nz]), each >= 2.
+ *   h, hbar  grid spacing and the Schroedinger parameter hbar (> 0).
+ *   f        N = prod(dims) forcing values, finite and > 0 (checked on the
+ *            device; failure returns EIK_ERR_ARG).
+ *   src_idx  nsrc flat node indices in [0, N) (nsrc >= 1).  Duplicates with
+ *            equal values are merged; duplicates with different values, or
+ *            indices out of range, return EIK_ERR_ARG.
+ *   src_U    nsrc prescribed values of S at the sources, or NULL for zeros.
+ *   opt      options, or NULL for eik_default_options().
+ *   stream   CUDA stream whose work orders the library's work (may be NULL for
+ *            the legacy default stream).
+ * Allocates device memory proportional to N (about 7 float64 vectors; the
+ * mixed mode adds about 5 float32 vectors).  Returns EIK_ERR_OOM if that
+ * fails.
+ */
+eik_status eik_create(eik_handle **out, int ndim, const int64_t *dims,
+                      double h, double hbar, const double *f,
+                      const int64_t *src_idx, const double *src_U,
+                      int64_t nsrc, const eik_options *opt,
+                      eik_stream_t stream);
+
+/* Replaces the forcing field (same validation as eik_create).  Sources, h
+ * and hbar are kept.  Invalidates the state kept for eik_grad. */
+eik_status eik_set_f(eik_handle *h, const double *f);
+
+/*
+ * Solves the system and writes S = -hbar log(phi) (Sec. 4, Eq. SfromPhi) to
+ * S_out (N values; S = U exactly on the sources).  phi_out, if not NULL,
+ * receives phi * exp(U_min/hbar) with U_min = min_k U_k (equal to phi when all
+ * U_k = 0), which lies in (0, 1].  stats may be NULL.  On
+ * EIK_ERR_NOT_CONVERGED the outputs hold the last iterate.
+ */
+eik_status eik_solve(eik_handle *h, double *S_out, double *phi_out,
+                     eik_stats *stats);
+
+/*
+ * Adjoint gradient of a loss L(S) with respect to f, after a successful
+ * eik_solve with the current f: dLdS (N values) in, dLdf (N values) out.
+ * With A(f) phi = b and A_ii = w_i f_i^2 + ..., dL/df_i = -2 w_i f_i phi_i
+ * lambda_i where A lambda = dL/dphi = -hbar (dL/dS)/phi; dLdf is 0 on the
+ * sources.  Returns EIK_ERR_STATE if no solve result is held.
+ */
+eik_status eik_grad(eik_handle *h, const double *dLdS, double *dLdf,
+                    eik_stats *stats);
+
+/* Releases the handle and its device memory.  NULL is accepted. */
+eik_status eik_destroy(eik_handle *h);
+
+/* Thread-local description of the last error (never NULL). */
+const char *eik_last_error(void);
+
+/* Library version (EIK_ABI_VERSION) and the CUDA architecture compiled for
+ * (e.g. 1030 for sm_103a). */
+int eik_abi_version(void);
+int eik_cuda_arch(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EIK_H_ */

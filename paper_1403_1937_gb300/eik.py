@@ -1,0 +1,198 @@
+"""Python binding with the names of the C ABI (``include/eik.h``).
+
+Arrays may be torch tensors (CUDA or CPU) or numpy arrays; they must be
+contiguous float64 (int64 for source indices).  Device tensors are passed to
+the library as device pointers, host arrays as host pointers; the library
+copies host data itself.  Work is ordered on ``torch.cuda.current_stream()``
+unless another stream is given.  This module only marshals arguments; the
+solve runs in libeik.so.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import _lib
+
+try:  # torch provides device memory and streams; optional for host use
+    import torch
+except Exception:  # pragma: no cover
+    torch = None
+
+
+def _is_torch(a) -> bool:
+    return torch is not None and isinstance(a, torch.Tensor)
+
+
+def _ptr(a, dtype, name: str):
+    """(pointer, keepalive) for a contiguous array of ``dtype``."""
+    if a is None:
+        return None, None
+    if _is_torch(a):
+        want = torch.float64 if dtype == np.float64 else torch.int64
+        if a.dtype != want:
+            raise TypeError(f"{name} must be {want}")
+        if not a.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        return ctypes.c_void_p(a.data_ptr()), a
+    arr = np.asarray(a)
+    if arr.dtype != dtype:
+        raise TypeError(f"{name} must be {np.dtype(dtype).name}")
+    if not arr.flags.c_contiguous:
+        raise ValueError(f"{name} must be C-contiguous")
+    return ctypes.c_void_p(arr.ctypes.data), arr
+
+
+def _numel(a) -> int:
+    return int(a.numel()) if _is_torch(a) else int(np.asarray(a).size)
+
+
+def _stream_ptr(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+    if torch is not None and torch.cuda.is_available():
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+def make_options(precision: str = "fp64", tol: Optional[float] = None,
+                 stop_norm: str = "componentwise", max_iter: Optional[int] = None,
+                 boundary: str = "half_cell", inner_tol: float = 0.0,
+                 max_outer: int = 0) -> _lib.Options:
+    o = _lib.default_options()
+    o.precision = {"fp64": _lib.PREC_FP64, "mixed": _lib.PREC_MIXED}[precision]
+    if tol is not None:
+        o.tol = float(tol)
+    o.stop_norm = {"componentwise": _lib.STOP_COMPONENTWISE,
+                   "normwise": _lib.STOP_NORMWISE}[stop_norm]
+    if max_iter is not None:
+        o.max_iter = int(max_iter)
+    o.boundary = {"half_cell": _lib.BOUNDARY_HALF_CELL,
+                  "drop_edge": _lib.BOUNDARY_DROP_EDGE}[boundary]
+    o.inner_tol = float(inner_tol)
+    o.max_outer = int(max_outer)
+    return o
+
+
+class Handle:
+    """Owns one ``eik_handle``; see ``eik_create``."""
+
+    def __init__(self, ptr: ctypes.c_void_p, dims: Tuple[int, ...], device: bool):
+        self._ptr = ptr
+        self.dims = dims
+        self.n = int(np.prod(dims))
+        self.device = device
+
+    @property
+    def ptr(self):
+        if not self._ptr:
+            raise RuntimeError("handle already destroyed")
+        return self._ptr
+
+    def __del__(self):
+        try:
+            eik_destroy(self)
+        except Exception:
+            pass
+
+
+def eik_create(dims: Sequence[int], h: float, hbar: float, f, src_idx, src_U=None,
+               options: Optional[_lib.Options] = None, stream=None) -> Handle:
+    """Creates a solver (C: ``eik_create``).  ``dims`` is (nx, ny[, nz]);
+    ``f`` holds prod(dims) float64 values in C order with x fastest."""
+    lib = _lib.load()
+    dims = tuple(int(d) for d in dims)
+    n = int(np.prod(dims))
+    if _numel(f) != n:
+        raise ValueError("f must have prod(dims) elements")
+    if not _is_torch(src_idx):
+        src_idx = np.ascontiguousarray(np.asarray(src_idx, dtype=np.int64).ravel())
+    if src_U is not None and not _is_torch(src_U):
+        src_U = np.ascontiguousarray(np.asarray(src_U, dtype=np.float64).ravel())
+    fp, fk = _ptr(f, np.float64, "f")
+    sp, sk = _ptr(src_idx, np.int64, "src_idx")
+    up, uk = _ptr(src_U, np.float64, "src_U")
+    if src_U is not None and _numel(src_U) != _numel(src_idx):
+        raise ValueError("src_U must match src_idx")
+    darr = (ctypes.c_int64 * len(dims))(*dims)
+    out = ctypes.c_void_p()
+    opt = options if options is not None else _lib.default_options()
+    st = lib.eik_create(ctypes.byref(out), len(dims), darr, float(h), float(hbar), fp, sp,
+                        up, _numel(src_idx), ctypes.byref(opt), _stream_ptr(stream))
+    _lib.check(st)
+    return Handle(out, dims, _is_torch(f) and f.is_cuda)
+
+
+def eik_set_f(handle: Handle, f) -> None:
+    """Replaces the forcing field (C: ``eik_set_f``)."""
+    if _numel(f) != handle.n:
+        raise ValueError("f must have prod(dims) elements")
+    fp, fk = _ptr(f, np.float64, "f")
+    _lib.check(_lib.load().eik_set_f(handle.ptr, fp))
+
+
+def _out_like(handle: Handle, out, like_device: bool):
+    if out is not None:
+        if _numel(out) != handle.n:
+            raise ValueError("output must have prod(dims) elements")
+        return out
+    if like_device and torch is not None:
+        return torch.empty(handle.dims[::-1], dtype=torch.float64, device="cuda")
+    return np.empty(handle.dims[::-1], dtype=np.float64)
+
+
+def eik_solve(handle: Handle, S_out=None, phi_out=None, want_phi: bool = False,
+              allow_not_converged: bool = False):
+    """Solves and returns (S, phi or None, stats dict) (C: ``eik_solve``).
+    Outputs are allocated like the inputs (CUDA tensors for a device handle,
+    numpy arrays otherwise) unless given."""
+    S_out = _out_like(handle, S_out, handle.device)
+    if want_phi or phi_out is not None:
+        phi_out = _out_like(handle, phi_out, handle.device)
+    sp, sk = _ptr(S_out, np.float64, "S_out")
+    pp, pk = _ptr(phi_out, np.float64, "phi_out")
+    stats = _lib.Stats()
+    st = _lib.load().eik_solve(handle.ptr, sp, pp, ctypes.byref(stats))
+    allow = (_lib.EIK_OK, _lib.EIK_ERR_NOT_CONVERGED) if allow_not_converged else (_lib.EIK_OK,)
+    _lib.check(st, allow)
+    d = stats.as_dict()
+    d["status"] = st
+    return S_out, phi_out, d
+
+
+def eik_grad(handle: Handle, dLdS, dLdf_out=None):
+    """Adjoint gradient dL/df for a loss L(S) of the last solve (C:
+    ``eik_grad``).  Returns (dLdf, stats dict)."""
+    if _numel(dLdS) != handle.n:
+        raise ValueError("dLdS must have prod(dims) elements")
+    dLdf_out = _out_like(handle, dLdf_out, _is_torch(dLdS) and dLdS.is_cuda)
+    ip, ik = _ptr(dLdS, np.float64, "dLdS")
+    op, ok = _ptr(dLdf_out, np.float64, "dLdf")
+    stats = _lib.Stats()
+    st = _lib.load().eik_grad(handle.ptr, ip, op, ctypes.byref(stats))
+    _lib.check(st)
+    return dLdf_out, stats.as_dict()
+
+
+def eik_destroy(handle: Handle) -> None:
+    """Releases the handle (C: ``eik_destroy``); safe to call twice."""
+    if handle is not None and handle._ptr:
+        _lib.load().eik_destroy(handle._ptr)
+        handle._ptr = None
+
+
+def solve(f, h: float, hbar: float, src_idx, src_U=None, precision: str = "fp64",
+          tol: Optional[float] = None, want_phi: bool = False, **kw):
+    """One-shot convenience: dims are taken from the array shape (numpy order
+    (nz,) ny, nx)."""
+    shape = tuple(f.shape)
+    dims = tuple(reversed(shape))
+    opt = make_options(precision=precision, tol=tol, **kw)
+    hd = eik_create(dims, h, hbar, f, src_idx, src_U, opt)
+    try:
+        S, phi, stats = eik_solve(hd, want_phi=want_phi)
+    finally:
+        eik_destroy(hd)
+    return S, phi, stats
