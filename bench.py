@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 screened-Poisson eikonal solve.
+
+Workload (default): 2D 2048 x 2048 grid on [0,1]^2 (h = 1/2047), smooth
+forcing f in [0.5, 1.5] from 8 seeded Fourier modes, 16 seeded random source
+nodes, hbar = 0.005 (seeded synthetic input; the paper's maze / image
+workloads are not available).  One step = one full solve through the C ABI:
+eik_set_f (setup of the scaled operator) + eik_solve (Jacobi-PCG to the
+componentwise tolerance, restarts, log epilogue).
+
+Metric: stencil-PCG GLUPS = sum over steps of (unknowns x CG iterations) /
+device seconds / 1e9, plus time-to-solution per step.  Both precision modes
+are timed; the headline line reports the mode given by --precision.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "stencil-PCG GLUPS and solve time, mixed vs FP64 plain at S err<=1e-6; %HBM peak"
+UNIT = "GLUPS"
+
+# Algorithmic bytes per grid node for one launch of each CG kernel
+# ("Kernels and their rooflines").
+ALGO_BYTES_PER_NODE = {
+    "cg_pass1_64": 32,   # read r, p, sig; write q            (4 x 8 B)
+    "cg_pass2_64": 56,   # read x, r, p, q; write x, r, p     (7 x 8 B)
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3"])
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-iters", type=int, default=0,
+                    help="oracle CG iterations in the CPU sample (0: sized to ~15 s)")
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_1403_1937_gb300 import workloads as wl
+    if name == "c2":
+        inst = wl.config2()
+        desc = {"workload": "2D 2048x2048 screened-Poisson eikonal, Fourier f in [0.5,1.5], "
+                            "16 sources, hbar=0.005", "grid": [2048, 2048], "sources": 16,
+                "hbar": 0.005}
+    else:
+        inst = wl.config3()
+        desc = {"workload": "3D 256^3 screened-Poisson eikonal, box f in [0.5,2], "
+                            "4 sources, hbar=0.02", "grid": [256, 256, 256], "sources": 4,
+                "hbar": 0.02}
+    return inst, desc
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1403_1937_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, workload_name):
+    """DRAM bytes per launch of ``kernel`` from the committed ncu summary, or
+    None when absent or taken on a different kernel source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    e = d.get(f"{kernel}@{workload_name}")
+    if not e or e.get("source_sha") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.device)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.samples = []
+        if self.proc is None:
+            return
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def summary(self):
+        if not getattr(self, "samples", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for k, v in zip(names, s[5:9]):
+                if v.lower() == "active":
+                    reasons.add(k)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.samples)}
+
+
+def flush_l2(buf):
+    buf.add_(1.0)   # 256 MiB write, larger than the 129 MB L2
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1403_1937_gb300 import build as _build
+    if not _build.up_to_date():
+        _build.build()
+    from paper_1403_1937_gb300 import eik
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl")
+    inst, desc = workload(args.workload)
+    n_unk = inst.n - len(np.unique(inst.src_idx))
+    f_host = torch.from_numpy(np.ascontiguousarray(inst.f)).pin_memory()
+    f_dev = f_host.cuda()
+    src = torch.from_numpy(inst.src_idx).cuda()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def make(prec):
+        opt = eik.make_options(precision=prec, tol=args.tol)
+        return eik.eik_create(inst.dims, inst.h, inst.hbar, f_dev, src, None, opt)
+
+    modes = [args.precision] + [m for m in ("fp64", "mixed") if m != args.precision]
+    results = {}
+    S_dev = torch.empty(inst.dims[::-1], dtype=torch.float64, device="cuda")
+    for mode in modes:
+        try:
+            hd = make(mode)
+        except Exception as e:  # mixed may be unavailable in this build
+            results[mode] = {"error": str(e).splitlines()[0]}
+            continue
+        for _ in range(args.warmup):
+            eik.eik_set_f(hd, f_dev)
+            eik.eik_solve(hd, S_out=S_dev)
+        torch.cuda.synchronize()
+        eik.eik_reset_kernel_stats(hd)
+        times, iters = [], []
+        if ws > 1:
+            dist.barrier()
+        with Clocks(local) as clk:
+            for _ in range(args.steps):
+                flush_l2(flush)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                eik.eik_set_f(hd, f_dev)
+                _, _, st = eik.eik_solve(hd, S_out=S_dev)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1) / 1e3)
+                iters.append(st["inner_iters"])
+        kst = eik.eik_kernel_stats(hd)
+        launches = sum(v[0] for v in kst.values())
+        total_t = sum(times)
+        if ws > 1:
+            t = torch.tensor([total_t], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_t = float(t.item())
+        units = n_unk * sum(iters) * ws
+        res = {"glups": units / total_t / 1e9, "ms_per_step": 1e3 * total_t / args.steps,
+               "cg_iters_per_step": statistics.mean(iters), "gpu_launches": launches,
+               "clocks": clk.summary(), "stats_last": st}
+        # end to end through host buffers (pinned), copies inside the timed region
+        if not args.no_e2e:
+            S_host = torch.empty(inst.dims[::-1], dtype=torch.float64).pin_memory()
+            eik.eik_set_f(hd, f_host.numpy())
+            eik.eik_solve(hd, S_out=S_host.numpy())
+            t0 = time.perf_counter()
+            e_iters = 0
+            for _ in range(args.steps):
+                eik.eik_set_f(hd, f_host.numpy())
+                _, _, st2 = eik.eik_solve(hd, S_out=S_host.numpy())
+                e_iters += st2["inner_iters"]
+            e_t = time.perf_counter() - t0
+            res["e2e"] = {"value": n_unk * e_iters * ws / e_t / 1e9, "unit": UNIT,
+                          "h2d_bytes_per_step": int(inst.n * 8),
+                          "d2h_bytes_per_step": int(inst.n * 8)}
+        # one more identical step with per-launch CUDA-event timing
+        eik.eik_reset_kernel_stats(hd)
+        eik.eik_set_profiling(hd, True)
+        eik.eik_set_f(hd, f_dev)
+        eik.eik_solve(hd, S_out=S_dev)
+        eik.eik_set_profiling(hd, False)
+        prof = eik.eik_kernel_stats(hd)
+        res["kernel_ms"] = {k: (v[2] / v[1] if v[1] else None, v[1], v[2])
+                            for k, v in prof.items() if v[0]}
+        results[mode] = res
+        eik.eik_destroy(hd)
+    if ws > 1:
+        dist.barrier()
+    return inst, desc, n_unk, results, ws, rank
+
+
+def roofline(res, inst, wname):
+    peak, peak_src = measured_peaks()
+    km = {k: v for k, v in res["kernel_ms"].items() if v[0] is not None}
+    cand = {k: v for k, v in km.items() if k in ALGO_BYTES_PER_NODE}
+    if not cand:
+        return None
+    dom = max(cand, key=lambda k: cand[k][2])
+    avg_ms = cand[dom][0]
+    algo = ALGO_BYTES_PER_NODE[dom] * inst.n
+    achieved = algo / (avg_ms * 1e-3) / 1e9
+    total = sum(v[2] for v in km.values())
+    return {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
+            "peak": peak, "peak_source": peak_src, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": ncu_traffic(dom, wname),
+            "algorithmic_bytes_per_launch": algo, "avg_launch_ms": avg_ms,
+            "share_of_kernel_time": round(cand[dom][2] / total, 3) if total else None}
+
+
+def cpu_baseline(inst, iters):
+    from oracle import cg, fd
+    sysm = fd.assemble(inst.f, inst.dims, inst.h, inst.hbar, inst.src_idx)
+    thr = cg.threads()
+    if iters <= 0:
+        t1 = cg.time_iterations(sysm, 5)
+        iters = int(max(10, min(2000, 15.0 / max(t1 / 5, 1e-6))))
+    t = cg.time_iterations(sysm, iters)
+    n_unk = len(sysm.unk)
+    return {"value": n_unk * iters / t / 1e9, "unit": UNIT, "cores": thr, "kind": "oracle",
+            "sample": f"{iters} Jacobi-PCG iterations of the C/OpenMP oracle on the full "
+                      f"{'x'.join(map(str, inst.dims))} system ({n_unk} unknowns), "
+                      f"{t:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle timed on the host cores (rank 0 only)."""
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    from oracle import cg, fd
+    inst, desc = workload(args.workload)
+    sysm = fd.assemble(inst.f, inst.dims, inst.h, inst.hbar, inst.src_idx)
+    n_unk = len(sysm.unk)
+    thr = cg.threads()
+    t1 = cg.time_iterations(sysm, 3) / 3
+    per_step = int(max(5, min(500, 4.0 / max(t1, 1e-6))))
+    for _ in range(args.warmup):
+        cg.time_iterations(sysm, per_step)
+    times = [cg.time_iterations(sysm, per_step) for _ in range(args.steps)]
+    total = sum(times)
+    value = n_unk * per_step * args.steps / total / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(desc, sample=f"{per_step} CG iterations per step"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
+                             "sample": f"{per_step} Jacobi-PCG iterations per step of the "
+                                       f"C/OpenMP oracle on the full system ({n_unk} "
+                                       f"unknowns)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    inst, desc, n_unk, results, ws, rank = run_ours(args)
+    if rank != 0:
+        return
+    head = results.get(args.precision, {})
+    if "glups" not in head:
+        print(json.dumps({"metric": METRIC, "error": head.get("error", "failed")}), flush=True)
+        sys.exit(1)
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_baseline(inst, args.cpu_iters)
+    comparison = {}
+    for mode, r in results.items():
+        if "glups" in r:
+            comparison[mode] = {"glups": round(r["glups"], 3),
+                                "ms_per_step": round(r["ms_per_step"], 3),
+                                "cg_iters_per_step": r["cg_iters_per_step"],
+                                "res_cw": r["stats_last"]["res_cw"]}
+        else:
+            comparison[mode] = r
+    if "glups" in results.get("fp64", {}) and "glups" in results.get("mixed", {}):
+        comparison["mixed_speedup_vs_fp64"] = round(
+            results["fp64"]["ms_per_step"] / results["mixed"]["ms_per_step"], 3)
+    line = {
+        "metric": METRIC, "value": round(head["glups"], 4), "unit": UNIT,
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(head["ms_per_step"], 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "data": "synthetic",
+        "config": dict(desc, precision=args.precision, tol_componentwise=args.tol,
+                       l2="flushed between steps (256 MiB write)",
+                       parallelism="replicas" if ws > 1 else "single GPU"),
+        "e2e": head.get("e2e"),
+        "gpu_launches": head["gpu_launches"],
+        "clocks": head["clocks"],
+        "roofline": roofline(head, inst, args.workload),
+        "cpu_baseline": cpu,
+        "comparison": comparison,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

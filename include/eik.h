@@ -154,6 +154,25 @@ eik_status eik_solve(eik_handle *h, double *S_out, double *phi_out,
 eik_status eik_grad(eik_handle *h, const double *dLdS, double *dLdf,
                     eik_stats *stats);
 
+/* Per-kernel counters of a handle (diagnostics; the paper has no
+ * counterpart).  launches counts every kernel launch the handle issued since
+ * creation or the last eik_reset_kernel_stats (kernels inside captured graphs
+ * count once per graph launch).  total_ms is the summed device time of those
+ * launches measured with CUDA events on the library's stream; it is filled
+ * only for launches made while profiling is enabled (eik_set_profiling),
+ * which replaces graph launches by individually timed launches. */
+typedef struct {
+  char name[32];
+  int64_t launches;
+  int64_t timed_launches;
+  double total_ms;
+} eik_kernel_stat;
+
+eik_status eik_set_profiling(eik_handle *h, int enable);
+/* Writes up to max entries to out and the number of kernels to *count. */
+eik_status eik_kernel_stats(eik_handle *h, eik_kernel_stat *out, int max, int *count);
+eik_status eik_reset_kernel_stats(eik_handle *h);
+
 /* Releases the handle and its device memory.  NULL is accepted. */
 eik_status eik_destroy(eik_handle *h);
 

@@ -196,6 +196,72 @@ def solve(f, dims, h, hbar, src_idx, src_U=None, boundary=0):
     return S_from_phi(sys, phi), phi, sys
 
 
+def graph_distance(sys: System) -> np.ndarray:
+    """Shortest-path distance from the sources over the grid graph with the
+    axis and diagonal neighbours of every node (edge cost: Euclidean length
+    times the mean of f at the two ends), plus the source values U - U_min.
+    Computed with scipy's Dijkstra; used only as a scale for the relative
+    solve below, never as the answer."""
+    from scipy.sparse import csgraph
+    dims = sys.dims
+    n = sys.n
+    idx = np.arange(n).reshape(dims[::-1])
+    rows, cols, vals = [], [], []
+    nd = len(dims)
+    import itertools
+    for off in itertools.product((-1, 0, 1), repeat=nd):
+        if all(o == 0 for o in off) or off[::-1] < tuple([0] * nd):
+            continue
+        sl_a, sl_b = [], []
+        for o in off:                       # numpy axis order matches off
+            sl_a.append(slice(max(-o, 0), None if o <= 0 else -o))
+            sl_b.append(slice(max(o, 0), None if o >= 0 else o))
+        a = idx[tuple(sl_a)].ravel()
+        b = idx[tuple(sl_b)].ravel()
+        length = sys.h * np.sqrt(sum(o * o for o in off))
+        w = length * 0.5 * (sys.f[a] + sys.f[b])
+        rows += [a, b]
+        cols += [b, a]
+        vals += [w, w]
+    G = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(n, n))
+    # a super-source joined to every source with cost U - U_min
+    G = sp.bmat([[G, None], [None, sp.csr_matrix((1, 1))]], format="lil")
+    for s_, u in zip(sys.src, sys.U):
+        G[n, s_] = u - sys.U_min + 1e-300
+    d = csgraph.dijkstra(G.tocsr(), directed=True, indices=n)
+    return d[:n]
+
+
+def solve_relative(sys: System, S_scale: Optional[np.ndarray] = None):
+    """Direct solve of the same system in relative form, for problems whose
+    phi underflows float64 (S/hbar > ~700).
+
+    With D = diag(exp(-St/hbar)) for any finite scale St (default: the graph
+    distance above), phi = D psi and the diagonally similar system
+    (D^-1 A D) psi = D^-1 b has entries A_ij exp((St_i - St_j)/hbar), which
+    stay O(1) between neighbours.  It is solved by sparse LU (it is no longer
+    symmetric), and S = U_min + St - hbar log(psi).  In exact arithmetic this
+    is the same solution as ``solve_phi``.  Returns S on the full grid."""
+    St = graph_distance(sys) if S_scale is None else np.asarray(S_scale, float).ravel()
+    u = sys.unk
+    A = sys.A.tocoo()
+    Su = St[u]
+    data = A.data * np.exp((Su[A.row] - Su[A.col]) / sys.hbar)
+    Ar = sp.csc_matrix((data, (A.row, A.col)), shape=A.shape)
+    # b_i / D_i = sum_{k in Y} c omega_ik exp(-(U_k - U_min)/hbar + St_i/hbar)
+    K = sys.K[u][:, sys.src].tocoo()
+    br = np.zeros(len(u))
+    np.add.at(br, K.row, -K.data * np.exp((Su[K.row] - (sys.U[K.col] - sys.U_min))
+                                          / sys.hbar))
+    lu = spla.splu(Ar, permc_spec="MMD_AT_PLUS_A", diag_pivot_thresh=0.0)
+    psi = lu.solve(br)
+    S = np.empty(sys.n)
+    S[u] = sys.U_min + Su - sys.hbar * np.log(psi)
+    S[sys.src] = sys.U
+    return S
+
+
 def componentwise_residual(sys: System, phi: np.ndarray) -> np.ndarray:
     """|r_i| / (a_i |phi_i|) on the unknowns for a full-grid phi (shifted),
     with r = b - A phi restricted to the unknowns."""

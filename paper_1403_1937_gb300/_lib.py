@@ -51,6 +51,11 @@ class Stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64),
+                ("timed_launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
 class EikError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -70,6 +75,9 @@ _SIGS = [
     ("eik_solve", ctypes.c_int, [_P, _P, _P, ctypes.POINTER(Stats)]),
     ("eik_grad", ctypes.c_int, [_P, _P, _P, ctypes.POINTER(Stats)]),
     ("eik_destroy", ctypes.c_int, [_P]),
+    ("eik_set_profiling", ctypes.c_int, [_P, ctypes.c_int]),
+    ("eik_kernel_stats", ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    ("eik_reset_kernel_stats", ctypes.c_int, [_P]),
     ("eik_last_error", ctypes.c_char_p, []),
     ("eik_abi_version", ctypes.c_int, []),
     ("eik_cuda_arch", ctypes.c_int, []),

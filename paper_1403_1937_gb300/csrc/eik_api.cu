@@ -49,6 +49,21 @@ bool is_device_pointer(const void *p) {
 constexpr int kGraphIters = 32;     // CG iterations per graph launch
 constexpr int kMaxRestarts = 4;     // restarts from the true residual
 
+// Kernels counted per handle (eik_kernel_stats).
+enum KernelId {
+  K_SETUP64 = 0, K_SOURCES64, K_RESIDUAL64, K_PASS1_64, K_PASS2_64, K_EPILOGUE64,
+  K_SOURCE_VALUES, K_ADJ_RHS64, K_ADJ_GRAD64, K_MIXED_FIRST
+};
+constexpr int kMaxKernels = 32;
+const char *const kKernelNames[K_MIXED_FIRST] = {
+    "setup64", "sources64", "residual64", "cg_pass1_64", "cg_pass2_64", "epilogue64",
+    "source_values", "adjoint_rhs64", "adjoint_grad64"};
+
+struct KernelStat {
+  int64_t launches = 0, timed = 0;
+  double ms = 0.0;
+};
+
 }  // namespace
 
 struct eik_handle {
@@ -78,6 +93,11 @@ struct eik_handle {
   } graphs[2];
   bool have_solution = false;
   MixedState *mixed = nullptr;
+  // diagnostics
+  KernelStat kstat[kMaxKernels];
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, int>> pending;   // (kernel id, event pair index)
 };
 
 namespace {
@@ -101,8 +121,45 @@ void free_handle(eik_handle *h) {
   cudaEvent_t evs[] = {h->ev_in, h->ev_out, h->ev_t0, h->ev_t1};
   for (cudaEvent_t e : evs)
     if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   if (h->stream) cudaStreamDestroy(h->stream);
   delete h;
+}
+
+void count_launch(eik_handle *h, int id, int64_t n = 1) { h->kstat[id].launches += n; }
+
+// Resolves the event pairs of timed launches (call after a stream sync).
+void flush_timed(eik_handle *h) {
+  for (auto &pr : h->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev_pool[2 * pr.second], h->ev_pool[2 * pr.second + 1]) ==
+        cudaSuccess) {
+      h->kstat[pr.first].ms += ms;
+      h->kstat[pr.first].timed += 1;
+    }
+  }
+  h->pending.clear();
+}
+
+// Launches fn() on the internal stream, counting it and, when profiling,
+// bracketing it with CUDA events.
+template <class F>
+void launch_k(eik_handle *h, int id, F fn) {
+  count_launch(h, id);
+  if (!h->profiling) {
+    fn();
+    return;
+  }
+  const int pair = (int)h->pending.size();
+  while ((int)h->ev_pool.size() < 2 * (pair + 1)) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    h->ev_pool.push_back(e);
+  }
+  CK(cudaEventRecord(h->ev_pool[2 * pair], h->stream));
+  fn();
+  CK(cudaEventRecord(h->ev_pool[2 * pair + 1], h->stream));
+  h->pending.push_back({id, pair});
 }
 
 template <class T>
@@ -136,8 +193,10 @@ void copy_in(eik_handle *h, double *dst, const double *src, int64_t n) {
 eik_status upload_f(eik_handle *h, const double *f) {
   copy_in(h, h->f, f, h->g.n);
   CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream));
-  launch_setup64(h->g, h->f, h->sig, h->x, h->err, h->stream, h->cap_elem);
-  launch_sources64(h->g, h->src, h->U, h->nsrc, h->sig, h->x, h->stream);
+  launch_k(h, K_SETUP64,
+           [&] { launch_setup64(h->g, h->f, h->sig, h->x, h->err, h->stream, h->cap_elem); });
+  launch_k(h, K_SOURCES64,
+           [&] { launch_sources64(h->g, h->src, h->U, h->nsrc, h->sig, h->x, h->stream); });
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(h->h_err, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
@@ -190,8 +249,10 @@ eik_status run_cg64(eik_handle *h, double *xs, const double *rhs, const double *
     init.iter = *iters;
     *h->h_st = init;
     CK(cudaMemcpyAsync(h->st, h->h_st, sizeof(CgState), cudaMemcpyHostToDevice, h->stream));
-    launch_residual64(h->g, h->tc, h->nblk_stencil, h->sig, xs, rhs, h->r, h->p, h->st,
-                      h->part, h->nblk_part, h->stream);
+    launch_k(h, K_RESIDUAL64, [&] {
+      launch_residual64(h->g, h->tc, h->nblk_stencil, h->sig, xs, rhs, h->r, h->p, h->st,
+                        h->part, h->nblk_part, h->stream);
+    });
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(CgState), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -210,12 +271,31 @@ eik_status run_cg64(eik_handle *h, double *xs, const double *rhs, const double *
     if (ok_now || h->h_st->rho == 0.0) return EIK_OK;
     if (*iters >= max_iter) return EIK_ERR_NOT_CONVERGED;
     if (restart > kMaxRestarts) return status == EIK_OK ? EIK_ERR_NOT_CONVERGED : status;
-    cudaGraphExec_t exec = graph_for(h, xs, weight);
+    cudaGraphExec_t exec = h->profiling ? nullptr : graph_for(h, xs, weight);
     for (;;) {
-      CK(cudaGraphLaunch(exec, h->stream));
+      if (exec) {
+        CK(cudaGraphLaunch(exec, h->stream));
+        count_launch(h, K_PASS1_64, kGraphIters);
+        count_launch(h, K_PASS2_64, kGraphIters);
+      } else {
+        // profiled: one iteration per host check, so no launch runs past
+        // convergence and every timed launch does the full pass
+        for (int k = 0; k < 1; ++k) {
+          launch_k(h, K_PASS1_64, [&] {
+            launch_pass1_64(h->g, h->tc, h->nblk_stencil, h->sig, h->r, h->p, h->q, h->st,
+                            h->part, h->nblk_part, h->stream);
+          });
+          launch_k(h, K_PASS2_64, [&] {
+            launch_pass2_64(h->g.n, h->nblk_stream, xs, h->r, h->p, h->q, weight, h->st,
+                            h->part + 8 * (size_t)h->nblk_part, h->nblk_part, h->stream);
+          });
+        }
+        CK(cudaGetLastError());
+      }
       CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(CgState), cudaMemcpyDeviceToHost,
                          h->stream));
       CK(cudaStreamSynchronize(h->stream));
+      flush_timed(h);
       if (h->h_st->done) break;
     }
     *iters = h->h_st->iter;
@@ -228,8 +308,10 @@ eik_status run_cg64(eik_handle *h, double *xs, const double *rhs, const double *
     }
     if (status == EIK_ERR_NOT_CONVERGED) {
       // report the true residual of the last iterate
-      launch_residual64(h->g, h->tc, h->nblk_stencil, h->sig, xs, rhs, h->r, h->p, h->st,
-                        h->part, h->nblk_part, h->stream);
+      launch_k(h, K_RESIDUAL64, [&] {
+        launch_residual64(h->g, h->tc, h->nblk_stencil, h->sig, xs, rhs, h->r, h->p, h->st,
+                          h->part, h->nblk_part, h->stream);
+      });
       CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(CgState), cudaMemcpyDeviceToHost,
                          h->stream));
       CK(cudaStreamSynchronize(h->stream));
@@ -244,13 +326,21 @@ eik_status run_cg64(eik_handle *h, double *xs, const double *rhs, const double *
 
 // Writes S (and phi) from the solution xh in h->x to the outputs, which may
 // be host or device pointers.
-void write_outputs(eik_handle *h, double *S_out, double *phi_out) {
+void write_outputs(eik_handle *h, double *S_out, double *phi_out,
+                   const MixedArgs *ma = nullptr) {
   const bool S_dev = is_device_pointer(S_out);
   const bool P_dev = phi_out ? is_device_pointer(phi_out) : true;
   double *S_d = S_dev ? S_out : h->aux;
   double *P_d = phi_out ? (P_dev ? phi_out : h->q) : nullptr;
-  launch_epilogue64(h->g, h->sig, h->x, S_d, P_d, h->stream, h->cap_elem);
-  launch_source_values(h->src, h->U, h->nsrc, S_d, h->stream);
+  if (ma) {
+    if (mixed_write_outputs(h->mixed, *ma, S_d, P_d) != EIK_OK)
+      throw CudaError{cudaErrorUnknown, "mixed epilogue"};
+  } else {
+    launch_k(h, K_EPILOGUE64,
+             [&] { launch_epilogue64(h->g, h->sig, h->x, S_d, P_d, h->stream, h->cap_elem); });
+  }
+  launch_k(h, K_SOURCE_VALUES,
+           [&] { launch_source_values(h->src, h->U, h->nsrc, S_d, h->stream); });
   CK(cudaGetLastError());
   if (!S_dev)
     CK(cudaMemcpyAsync(S_out, S_d, sizeof(double) * h->g.n, cudaMemcpyDeviceToHost,
@@ -467,8 +557,9 @@ eik_status eik_solve(eik_handle *h, double *S_out, double *phi_out, eik_stats *s
     int iters = 0, outer = 1;
     double res_cw = 0, res_nw = 0;
     eik_status s;
-    if (h->opt.precision == EIK_PREC_MIXED) {
-      MixedArgs ma{};
+    MixedArgs ma{};
+    const bool mixed = h->opt.precision == EIK_PREC_MIXED;
+    if (mixed) {
       ma.g = h->g;
       ma.tc = h->tc;
       ma.stream = h->stream;
@@ -492,14 +583,18 @@ eik_status eik_solve(eik_handle *h, double *S_out, double *phi_out, eik_stats *s
     } else {
       // reset the solution (sources keep their slots)
       CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream));
-      launch_setup64(h->g, h->f, h->sig, h->x, h->err, h->stream, h->cap_elem);
-      launch_sources64(h->g, h->src, h->U, h->nsrc, h->sig, h->x, h->stream);
+      launch_k(h, K_SETUP64,
+               [&] { launch_setup64(h->g, h->f, h->sig, h->x, h->err, h->stream, h->cap_elem); });
+      launch_k(h, K_SOURCES64,
+               [&] { launch_sources64(h->g, h->src, h->U, h->nsrc, h->sig, h->x, h->stream); });
       s = run_cg64(h, h->x, nullptr, nullptr, h->opt.tol, h->opt.stop_norm, h->opt.max_iter,
                    &iters, &res_cw, &res_nw);
     }
-    if (s == EIK_OK || s == EIK_ERR_NOT_CONVERGED) write_outputs(h, S_out, phi_out);
+    if (s == EIK_OK || s == EIK_ERR_NOT_CONVERGED)
+      write_outputs(h, S_out, phi_out, mixed ? &ma : nullptr);
     CK(cudaEventRecord(h->ev_t1, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    flush_timed(h);
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, h->ev_t0, h->ev_t1));
     if (stats) {
@@ -538,8 +633,10 @@ eik_status eik_grad(eik_handle *h, const double *dLdS, double *dLdf, eik_stats *
     if (!is_device_pointer(dLdS)) CK(cudaStreamSynchronize(h->stream));
     double *rhs = h->grhs;
     double *gmax_part = h->part + 12 * (size_t)h->nblk_part;
-    launch_adjoint_rhs64(h->g, h->sig, h->x, h->aux, rhs, gmax_part, h->nblk_stream,
-                         h->stream);
+    launch_k(h, K_ADJ_RHS64, [&] {
+      launch_adjoint_rhs64(h->g, h->sig, h->x, h->aux, rhs, gmax_part, h->nblk_stream,
+                           h->stream);
+    });
     std::vector<double> gm(h->nblk_stream);
     CK(cudaMemcpyAsync(gm.data(), gmax_part, sizeof(double) * h->nblk_stream,
                        cudaMemcpyDeviceToHost, h->stream));
@@ -559,13 +656,16 @@ eik_status eik_grad(eik_handle *h, const double *dLdS, double *dLdf, eik_stats *
     }
     const bool out_dev = is_device_pointer(dLdf);
     double *out_d = out_dev ? dLdf : h->aux;
-    launch_adjoint_grad64(h->g, h->f, h->sig, h->x, h->lam, out_d, h->stream, h->cap_elem);
+    launch_k(h, K_ADJ_GRAD64, [&] {
+      launch_adjoint_grad64(h->g, h->f, h->sig, h->x, h->lam, out_d, h->stream, h->cap_elem);
+    });
     CK(cudaGetLastError());
     if (!out_dev)
       CK(cudaMemcpyAsync(dLdf, out_d, sizeof(double) * h->g.n, cudaMemcpyDeviceToHost,
                          h->stream));
     CK(cudaEventRecord(h->ev_t1, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    flush_timed(h);
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, h->ev_t0, h->ev_t1));
     if (stats) {
@@ -581,6 +681,39 @@ eik_status eik_grad(eik_handle *h, const double *dLdS, double *dLdf, eik_stats *
     return fail(EIK_ERR_CUDA, std::string("CUDA error in ") + e.what + ": " +
                                   cudaGetErrorString(e.err));
   }
+}
+
+eik_status eik_set_profiling(eik_handle *h, int enable) {
+  if (!h) return fail(EIK_ERR_ARG, "NULL handle");
+  h->profiling = enable != 0;
+  return EIK_OK;
+}
+
+eik_status eik_kernel_stats(eik_handle *h, eik_kernel_stat *out, int max, int *count) {
+  if (!h || !count) return fail(EIK_ERR_ARG, "NULL handle or count");
+  int n = 0;
+  for (int id = 0; id < kMaxKernels; ++id) {
+    const char *name = id < K_MIXED_FIRST ? kKernelNames[id] : mixed_kernel_name(id - K_MIXED_FIRST);
+    if (!name) continue;
+    if (out && n < max) {
+      std::memset(out[n].name, 0, sizeof(out[n].name));
+      std::strncpy(out[n].name, name, sizeof(out[n].name) - 1);
+      out[n].launches = h->kstat[id].launches +
+                        (id >= K_MIXED_FIRST ? mixed_kernel_launches(h->mixed, id - K_MIXED_FIRST) : 0);
+      out[n].timed_launches = h->kstat[id].timed;
+      out[n].total_ms = h->kstat[id].ms;
+    }
+    ++n;
+  }
+  *count = n;
+  return EIK_OK;
+}
+
+eik_status eik_reset_kernel_stats(eik_handle *h) {
+  if (!h) return fail(EIK_ERR_ARG, "NULL handle");
+  for (auto &k : h->kstat) k = KernelStat{};
+  mixed_reset_launches(h->mixed);
+  return EIK_OK;
 }
 
 eik_status eik_destroy(eik_handle *h) {

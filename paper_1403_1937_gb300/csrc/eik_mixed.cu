@@ -1,22 +1,941 @@
-// Mixed-precision solve: placeholder until the FP32 kernels land.
+// Mixed-precision solve: FP32 inner CG with per-node block floating point,
+// FP64 iterative refinement in relative (exponent-scaled) form.
+//
+// Why the scaling: phi = exp(-S/hbar) spans exp(-max S/hbar), far below the
+// FP32 range (and, for S/hbar > ~700, below FP64).  Two exponents keep every
+// stored number in range:
+//   * kx(cell): a static power-of-two scale per cell of B^d nodes, rounded
+//     from a cheap distance estimate St ~ S (min-plus relaxation on the
+//     coarse cell grid, 16/26-neighbour stencil, edge cost = length x mean of
+//     the two cell-averaged f).  Solution-like vectors (the FP64 iterate xk and
+//     the FP32 correction d) are stored as hat-value * 2^kx(cell).
+//   * e(node): a per-node exponent shared by the FP32 residual r and search
+//     direction p of the inner CG, renormalised in every pass 2 so the larger
+//     of |r|, |p| lies in [1, 2).  Hat values are stored * 2^-e ... i.e.
+//     rhat = r * 2^-e.  This follows the residual's own decay, which spans far
+//     more than the FP32 range over an inner solve.
+// All rescaling is by powers of two, so it is exact; CG arithmetic is that of
+// Jacobi-preconditioned CG on the scaled operator Ahat (see eik_internal.cuh)
+// rounded to FP32 mantissas.  Inner products are accumulated as
+// (mantissa, exponent) pairs so they cannot underflow or overflow.
+//
+// The inner FP32 CG yields accurate values near the sources but not in the
+// far field: CG iterates there pass through transients many orders larger
+// than the final values, whose cancellation FP32 cannot carry.  Refinement
+// repairs this: each outer step forms the true FP64 residual in relative
+// form and solves for a correction with a fresh inner CG.
+#include <math.h>
+#include <stdio.h>
+
+#include <string>
+
+#include "eik_launch.h"
 #include "eik_mixed.h"
 
 namespace eik {
 
-struct MixedState {
-  int dummy;
+namespace {
+
+constexpr int kInnerGraphIters = 32;   // even: the buffer sets alternate
+constexpr int kNoExp = 30000;          // exponent of an all-zero node
+constexpr int kMaxCells = 16384;
+
+std::string g_msg = "no error";
+
+// ------------------------------------------------------------ exponents
+__device__ __forceinline__ float pow2f(int n) {
+  if (n < -126) return 0.f;
+  if (n > 127) n = 127;
+  return __int_as_float((n + 127) << 23);
+}
+__device__ __forceinline__ double pow2d(int n) {
+  if (n < -1022) return 0.0;
+  if (n > 1023) n = 1023;
+  return __longlong_as_double((long long)(n + 1023) << 52);
+}
+// floor(log2 |m|) for a finite non-zero normal float
+__device__ __forceinline__ int expof(float m) {
+  return ((__float_as_int(m) >> 23) & 0xff) - 127;
+}
+
+// (mantissa, exponent) accumulators: value = m * 2^s.
+struct Acc32 {
+  float m;
+  int s;
+};
+struct Acc64 {
+  double m;
+  int s;
+};
+__device__ __forceinline__ void acc_add(Acc32 &a, float m, int t) {
+  if (m == 0.f) return;
+  if (a.m == 0.f) {
+    a.m = m;
+    a.s = t;
+  } else if (t > a.s) {
+    a.m = a.m * pow2f(a.s - t) + m;
+    a.s = t;
+  } else {
+    a.m += m * pow2f(t - a.s);
+  }
+}
+__device__ __forceinline__ void acc_add(Acc64 &a, double m, int t) {
+  if (m == 0.0) return;
+  if (a.m == 0.0) {
+    a.m = m;
+    a.s = t;
+  } else if (t > a.s) {
+    a.m = a.m * pow2d(a.s - t) + m;
+    a.s = t;
+  } else {
+    a.m += m * pow2d(t - a.s);
+  }
+  // keep the mantissa near 1 so long sums cannot overflow
+  if (a.m != 0.0) {
+    int e;
+    const double fr = frexp(a.m, &e);
+    a.m = fr;
+    a.s += e;
+  }
+}
+__device__ __forceinline__ Acc64 to64(const Acc32 &a) {
+  Acc64 r{0.0, 0};
+  acc_add(r, (double)a.m, a.s);
+  return r;
+}
+// Deterministic block combine of Acc64 (valid in thread 0).
+__device__ Acc64 block_acc(Acc64 v, double *shm, int *shs) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const double m = __shfl_down_sync(0xffffffffu, v.m, o);
+    const int s = __shfl_down_sync(0xffffffffu, v.s, o);
+    acc_add(v, m, s);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) {
+    shm[w] = v.m;
+    shs[w] = v.s;
+  }
+  __syncthreads();
+  Acc64 r{0.0, 0};
+  if (w == 0) {
+    if (l < (int)(blockDim.x >> 5)) r = Acc64{shm[l], shs[l]};
+    for (int o = 16; o > 0; o >>= 1) {
+      const double m = __shfl_down_sync(0xffffffffu, r.m, o);
+      const int s = __shfl_down_sync(0xffffffffu, r.s, o);
+      acc_add(r, m, s);
+    }
+  }
+  return r;
+}
+__device__ float block_maxf(float v, float *sh) {
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  v = 0.f;
+  if (w == 0) {
+    v = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
+  }
+  return v;
+}
+// Fixed-order combine of per-block Acc64 partials (m in pm, s in ps).
+__device__ Acc64 sum_acc_partials(const double *pm, const double *ps, int nblk, double *shm,
+                                  int *shs) {
+  Acc64 v{0.0, 0};
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) acc_add(v, __ldcg(pm + b), (int)__ldcg(ps + b));
+  return block_acc(v, shm, shs);
+}
+__device__ __forceinline__ double acc_ratio(const Acc64 &a, const Acc64 &b) {
+  if (b.m == 0.0) return 0.0;
+  return (a.m / b.m) * pow2d(a.s - b.s);
+}
+
+// Inner-CG control block (device resident).
+struct MixState {
+  double rho_m;      // <rhat, rhat> = rho_m * 2^rho_s
+  int rho_s;
+  int iter;          // inner iterations of the current solve
+  double alpha, beta;
+  float thresh;      // stop when max_i |rhat_i| 2^kx(i) <= thresh
+  int max_iter;
+  int done;
+  int status;
+  int total_iter;
+  int pad;
+  unsigned int counter[4];
+  // outputs of the relative-form FP64 residual
+  double cw;         // max |r|/(a phi) over the unknowns
+  double r_inf;      // max |rbar64| (kx units)
+  double x_inf;      // max |xbar64| (kx units)
 };
 
-static const char *g_msg = "mixed precision is not available in this build";
+struct CellGrid {
+  int B, lgB;        // cell edge in nodes (power of two) and its log2
+  int cx, cy, cz;    // cells per axis
+  int ncell;
+};
 
-eik_status mixed_create(MixedState **out, const Grid &, const TileCount &, int, cudaStream_t) {
-  *out = nullptr;
-  return EIK_ERR_ARG;
+__device__ __forceinline__ int cell_of(const CellGrid &cg, int x, int y, int z) {
+  return (x >> cg.lgB) + cg.cx * ((y >> cg.lgB) + cg.cy * (z >> cg.lgB));
 }
-eik_status mixed_solve(MixedState *, const MixedArgs &, int *, int *, double *, double *) {
-  return EIK_ERR_ARG;
+
+template <int DIM>
+__device__ __forceinline__ void tile_origin_m(const TileCount &tc, int64_t t, int &x0, int &y0,
+                                              int &z0) {
+  using T = Tile<DIM>;
+  const int bx = (int)(t % tc.tx);
+  const int64_t r = t / tc.tx;
+  x0 = bx * T::TX;
+  y0 = (int)(r % tc.ty) * T::TY;
+  z0 = (int)(r / tc.ty) * T::TZ;
 }
-void mixed_destroy(MixedState *m) { delete m; }
-const char *mixed_last_error() { return g_msg; }
+
+// ----------------------------------------------------------- setup kernels
+__global__ void k_sig32(int64_t n, const double *__restrict__ sig, float *__restrict__ s32) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    s32[i] = (float)sig[i];
+}
+
+// Mean of f over each cell (one block per cell).
+__global__ void k_cell_mean(Grid g, CellGrid cg, const double *__restrict__ f,
+                            float *__restrict__ fb) {
+  __shared__ double red[32];
+  const int c = blockIdx.x;
+  const int I = c % cg.cx, J = (c / cg.cx) % cg.cy, K = c / (cg.cx * cg.cy);
+  const int x0 = I * cg.B, y0 = J * cg.B, z0 = K * cg.B;
+  const int x1 = min(x0 + cg.B, g.nx), y1 = min(y0 + cg.B, g.ny);
+  const int z1 = (g.ndim == 3) ? min(z0 + cg.B, g.nz) : 1;
+  const int wx = x1 - x0, wy = y1 - y0, wz = z1 - z0;
+  const int cnt = wx * wy * wz;
+  double s = 0.0;
+  for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+    const int lx = k % wx, ly = (k / wx) % wy, lz = k / (wx * wy);
+    s += f[(x0 + lx) + (int64_t)g.nx * ((y0 + ly) + (int64_t)g.ny * (z0 + lz))];
+  }
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) fb[c] = (float)(s / cnt);
+}
+
+// Distance estimate St on the cell grid by min-plus relaxation, then the
+// cell exponents kx = round(St / (hbar ln 2)).  One block; the cell grid is in
+// shared memory.  Converges in at most ncell sweeps (Bellman-Ford bound).
+__global__ void __launch_bounds__(1024)
+k_coarse_exponents(Grid g, CellGrid cg, double h, const float *__restrict__ fb_g,
+                   const int64_t *__restrict__ src, const double *__restrict__ U,
+                   int64_t nsrc, int *__restrict__ kx, float *__restrict__ St_out) {
+  extern __shared__ float smem[];
+  float *St = smem;
+  float *fb = smem + cg.ncell;
+  const int nc = cg.ncell;
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+    St[c] = INFINITY;
+    fb[c] = fb_g[c];
+  }
+  __syncthreads();
+  const float H = (float)(h * cg.B);
+  const int R = 2;
+  const int span = (g.ndim == 3) ? (2 * R + 1) * (2 * R + 1) * (2 * R + 1) : (2 * R + 1) * (2 * R + 1);
+  for (int64_t w = threadIdx.x; w < nsrc * span; w += blockDim.x) {
+    const int64_t k = w / span;
+    const int o = (int)(w % span);
+    const int64_t j = src[k];
+    const int sx = (int)(j % g.nx);
+    const int sy = (int)((j / g.nx) % g.ny);
+    const int sz = (int)(j / ((int64_t)g.nx * g.ny));
+    const int dI = o % (2 * R + 1) - R, dJ = (o / (2 * R + 1)) % (2 * R + 1) - R;
+    const int dK = (g.ndim == 3) ? o / ((2 * R + 1) * (2 * R + 1)) - R : 0;
+    const int I = (sx >> cg.lgB) + dI, J = (sy >> cg.lgB) + dJ, K = (sz >> cg.lgB) + dK;
+    if (I < 0 || I >= cg.cx || J < 0 || J >= cg.cy || K < 0 || K >= cg.cz) continue;
+    const float cxp = fminf(I * cg.B + 0.5f * (cg.B - 1), (float)(g.nx - 1));
+    const float cyp = fminf(J * cg.B + 0.5f * (cg.B - 1), (float)(g.ny - 1));
+    const float czp = (g.ndim == 3) ? fminf(K * cg.B + 0.5f * (cg.B - 1), (float)(g.nz - 1)) : 0.f;
+    const float dx = cxp - sx, dy = cyp - sy, dz = czp - sz;
+    const int c = I + cg.cx * (J + cg.cy * K);
+    const float v = (float)(U[k] - g.U_min) + fb[c] * (float)h * sqrtf(dx * dx + dy * dy + dz * dz);
+    atomicMin((int *)&St[c], __float_as_int(fmaxf(v, 0.f)));
+  }
+  __syncthreads();
+  // neighbour offsets: 2D axis + diagonal + knight (16); 3D the 26 of the cube
+  for (int sweep = 0; sweep <= nc + 1; ++sweep) {
+    int changed = 0;
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+      const int I = c % cg.cx, J = (c / cg.cx) % cg.cy, K = c / (cg.cx * cg.cy);
+      float best = St[c];
+      const float fc = fb[c];
+      if (g.ndim == 2) {
+        const int off[16][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1}, {1, 1}, {1, -1},
+                                {-1, 1}, {-1, -1}, {1, 2}, {2, 1}, {-1, 2}, {-2, 1},
+                                {1, -2}, {2, -1}, {-1, -2}, {-2, -1}};
+        for (int q = 0; q < 16; ++q) {
+          const int I2 = I + off[q][0], J2 = J + off[q][1];
+          if (I2 < 0 || I2 >= cg.cx || J2 < 0 || J2 >= cg.cy) continue;
+          const int c2 = I2 + cg.cx * J2;
+          const float len = sqrtf((float)(off[q][0] * off[q][0] + off[q][1] * off[q][1]));
+          best = fminf(best, St[c2] + H * len * 0.5f * (fc + fb[c2]));
+        }
+      } else {
+        for (int q = 0; q < 27; ++q) {
+          const int a = q % 3 - 1, b = (q / 3) % 3 - 1, d = q / 9 - 1;
+          if (!a && !b && !d) continue;
+          const int I2 = I + a, J2 = J + b, K2 = K + d;
+          if (I2 < 0 || I2 >= cg.cx || J2 < 0 || J2 >= cg.cy || K2 < 0 || K2 >= cg.cz) continue;
+          const int c2 = I2 + cg.cx * (J2 + cg.cy * K2);
+          const float len = sqrtf((float)(a * a + b * b + d * d));
+          best = fminf(best, St[c2] + H * len * 0.5f * (fc + fb[c2]));
+        }
+      }
+      if (best < St[c]) {
+        St[c] = best;
+        changed = 1;
+      }
+    }
+    if (!__syncthreads_or(changed)) break;
+  }
+  const float inv = (float)(1.0 / (g.hbar * 0.69314718055994530942));
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+    const float v = St[c];
+    kx[c] = isfinite(v) ? (int)rintf(v * inv) : 0;
+    if (St_out) St_out[c] = v;
+  }
+}
+
+// FP64 iterate: 0 on the unknowns, the shifted source values in kx units on
+// the sources: sqrt(c) phi_k 2^kx = sqrt(c) exp(kx ln2 - (U_k - U_min)/hbar).
+__global__ void k_init_x64(Grid g, CellGrid cg, const int *__restrict__ kx,
+                           const int64_t *__restrict__ src, const double *__restrict__ U,
+                           int64_t nsrc, double *__restrict__ x64) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nsrc) return;
+  const int64_t j = src[k];
+  const int sx = (int)(j % g.nx), sy = (int)((j / g.nx) % g.ny);
+  const int sz = (int)(j / ((int64_t)g.nx * g.ny));
+  const int kk = kx[cell_of(cg, sx, sy, sz)];
+  x64[j] = g.sqrt_c * exp(kk * 0.69314718055994530942 - (U[k] - g.U_min) / g.hbar);
+}
+
+// ----------------------------------------- FP64 residual in relative form
+// rbar_i = sig_i sum_j omega_ij 2^(kx_i - kx_j) u_j - xbar_i (kx units),
+// u_j = sig_j xbar_j (unknowns) or the source slot xbar_j.  Also initialises
+// the inner CG: BFP residual (mantissa + exponent) in buffer set 0, p = 0,
+// d = 0, and reduces rho = <rhat, rhat>, the componentwise residual
+// max |rbar|/xbar, max |rbar| and max |xbar| (kx units).
+template <int DIM>
+__global__ void __launch_bounds__(kThreads)
+k_mixed_residual(Grid g, TileCount tc, CellGrid cg, const int *__restrict__ kx,
+                 const double *__restrict__ sig, const double *__restrict__ x64,
+                 float *__restrict__ r32, float *__restrict__ p32, short *__restrict__ e16,
+                 float *__restrict__ d32, MixState *st, double *part, int nblk_part) {
+  using T = Tile<DIM>;
+  constexpr int HN = T::HX * T::HY * T::HZ;
+  constexpr int TN = T::TX * T::TY * T::TZ;
+  __shared__ double su[HN];
+  __shared__ int sk[HN];
+  __shared__ double shm[32];
+  __shared__ int shs[32];
+  __shared__ int flag;
+  Acc64 rho{0.0, 0};
+  double cwm = 0.0, rinf = 0.0, xinf = 0.0;
+  for (int64_t t = blockIdx.x; t < tc.total; t += gridDim.x) {
+    int x0, y0, z0;
+    tile_origin_m<DIM>(tc, t, x0, y0, z0);
+    for (int s = threadIdx.x; s < HN; s += blockDim.x) {
+      const int hx = s % T::HX, hy = (s / T::HX) % T::HY, hz = s / (T::HX * T::HY);
+      const int gx = x0 - 1 + hx, gy = y0 - 1 + hy, gz = (DIM == 3) ? z0 - 1 + hz : 0;
+      double u = 0.0;
+      int kk = 0;
+      if (gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny && gz >= 0 && gz < g.nz) {
+        const int64_t gi = gx + (int64_t)g.nx * (gy + (int64_t)g.ny * gz);
+        const double sj = sig[gi], xj = x64[gi];
+        u = (sj == 0.0) ? xj : sj * xj;
+        kk = kx[cell_of(cg, gx, gy, gz)];
+      }
+      su[s] = u;
+      sk[s] = kk;
+    }
+    __syncthreads();
+    for (int lin = threadIdx.x; lin < TN; lin += blockDim.x) {
+      const int lx = lin % T::TX, ly = (lin / T::TX) % T::TY, lz = lin / (T::TX * T::TY);
+      const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
+      if (gx >= g.nx || gy >= g.ny || gz >= g.nz) continue;
+      const int s = (DIM == 3 ? (lz + 1) * T::HX * T::HY : 0) + (ly + 1) * T::HX + lx + 1;
+      const int64_t gi = gx + (int64_t)g.nx * (gy + (int64_t)g.ny * gz);
+      const double si = sig[gi], xi = x64[gi];
+      const int ki = sk[s];
+      double rb = 0.0;
+      if (si != 0.0) {
+        const double hx = half_if(on_face(gx, g.nx, g.boundary));
+        const double hy = half_if(on_face(gy, g.ny, g.boundary));
+        double acc;
+        if (DIM == 2) {
+          acc = hy * (su[s - 1] * pow2d(ki - sk[s - 1]) + su[s + 1] * pow2d(ki - sk[s + 1])) +
+                hx * (su[s - T::HX] * pow2d(ki - sk[s - T::HX]) +
+                      su[s + T::HX] * pow2d(ki - sk[s + T::HX]));
+        } else {
+          const double hz = half_if(on_face(gz, g.nz, g.boundary));
+          constexpr int PL = T::HX * T::HY;
+          acc = hy * hz * (su[s - 1] * pow2d(ki - sk[s - 1]) + su[s + 1] * pow2d(ki - sk[s + 1])) +
+                hx * hz * (su[s - T::HX] * pow2d(ki - sk[s - T::HX]) +
+                           su[s + T::HX] * pow2d(ki - sk[s + T::HX])) +
+                hx * hy * (su[s - PL] * pow2d(ki - sk[s - PL]) + su[s + PL] * pow2d(ki - sk[s + PL]));
+        }
+        rb = si * acc - xi;
+        const double cw = (xi > 0.0) ? fabs(rb) / xi : INFINITY;
+        cwm = fmax(cwm, cw);
+        rinf = fmax(rinf, fabs(rb));
+        xinf = fmax(xinf, fabs(xi));
+      }
+      // BFP initial residual: rhat = rb 2^-ki = m 2^-e with m in [1, 2)
+      float m = 0.f;
+      int e = kNoExp;
+      if (rb != 0.0) {
+        int ex;
+        const double fr = frexp(rb, &ex);      // rb = fr 2^ex, |fr| in [0.5, 1)
+        m = (float)(2.0 * fr);
+        e = ki - (ex - 1);
+        acc_add(rho, (double)m * (double)m, -2 * e);
+      }
+      r32[gi] = m;
+      p32[gi] = 0.f;
+      e16[gi] = (short)max(-32000, min(e, 32000));
+      d32[gi] = 0.f;
+    }
+    __syncthreads();
+  }
+  const Acc64 tot = block_acc(rho, shm, shs);
+  const double c1 = block_max(cwm, shm);
+  const double c2 = block_max(rinf, shm);
+  const double c3 = block_max(xinf, shm);
+  if (threadIdx.x == 0) {
+    part[0 * nblk_part + blockIdx.x] = tot.m;
+    part[1 * nblk_part + blockIdx.x] = (double)tot.s;
+    part[2 * nblk_part + blockIdx.x] = c1;
+    part[3 * nblk_part + blockIdx.x] = c2;
+    part[4 * nblk_part + blockIdx.x] = c3;
+  }
+  if (!last_block(&st->counter[0], &flag)) return;
+  const Acc64 r = sum_acc_partials(part, part + nblk_part, gridDim.x, shm, shs);
+  const double cw = max_partials(part + 2 * nblk_part, gridDim.x, shm);
+  const double ri = max_partials(part + 3 * nblk_part, gridDim.x, shm);
+  const double xi = max_partials(part + 4 * nblk_part, gridDim.x, shm);
+  if (threadIdx.x == 0) {
+    st->rho_m = r.m;
+    st->rho_s = r.s;
+    st->cw = cw;
+    st->r_inf = ri;
+    st->x_inf = xi;
+    st->beta = 0.0;
+    st->counter[0] = 0u;
+  }
+}
+
+// ------------------------------------------------------------ inner CG
+// Stages ptil = r + beta p (per-node exponent e) with sig for the tile and
+// its halo; zero nodes carry e = kNoExp.
+template <int DIM>
+__device__ __forceinline__ void stage_p(const Grid &g, int x0, int y0, int z0, float beta,
+                                        const float *__restrict__ r32,
+                                        const float *__restrict__ p32,
+                                        const short *__restrict__ e16,
+                                        const float *__restrict__ s32, float *sp, int *se,
+                                        float *ss) {
+  using T = Tile<DIM>;
+  constexpr int HN = T::HX * T::HY * T::HZ;
+  for (int s = threadIdx.x; s < HN; s += blockDim.x) {
+    const int hx = s % T::HX, hy = (s / T::HX) % T::HY, hz = s / (T::HX * T::HY);
+    const int gx = x0 - 1 + hx, gy = y0 - 1 + hy, gz = (DIM == 3) ? z0 - 1 + hz : 0;
+    float pv = 0.f, sv = 0.f;
+    int ev = kNoExp;
+    if (gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny && gz >= 0 && gz < g.nz) {
+      const int64_t gi = gx + (int64_t)g.nx * (gy + (int64_t)g.ny * gz);
+      pv = fmaf(beta, p32[gi], r32[gi]);
+      ev = e16[gi];   // exponent of r and p at this node (kNoExp if both are 0)
+      sv = s32[gi];
+    }
+    sp[s] = pv;
+    se[s] = ev;
+    ss[s] = sv;
+  }
+}
+
+// q in units of E = min exponent of the stencil (the largest scale), so no
+// term can overflow: q = ptil_i 2^(E-e_i) - sig_i sum_j omega sig_j ptil_j 2^(E-e_j).
+template <int DIM>
+__device__ __forceinline__ float stencil_q(const Grid &g, const float *sp, const int *se,
+                                           const float *ss, int s, int gx, int gy, int gz,
+                                           int &E) {
+  using T = Tile<DIM>;
+  constexpr int PL = T::HX * T::HY;
+  const int ei = se[s];
+  int m = min(ei, min(min(se[s - 1], se[s + 1]), min(se[s - T::HX], se[s + T::HX])));
+  if (DIM == 3) m = min(m, min(se[s - PL], se[s + PL]));
+  E = m;
+  const float hx = on_face(gx, g.nx, g.boundary) ? 0.5f : 1.f;
+  const float hy = on_face(gy, g.ny, g.boundary) ? 0.5f : 1.f;
+  float acc;
+  if (DIM == 2) {
+    acc = hy * (ss[s - 1] * sp[s - 1] * pow2f(m - se[s - 1]) +
+                ss[s + 1] * sp[s + 1] * pow2f(m - se[s + 1])) +
+          hx * (ss[s - T::HX] * sp[s - T::HX] * pow2f(m - se[s - T::HX]) +
+                ss[s + T::HX] * sp[s + T::HX] * pow2f(m - se[s + T::HX]));
+  } else {
+    const float hz = on_face(gz, g.nz, g.boundary) ? 0.5f : 1.f;
+    acc = hy * hz * (ss[s - 1] * sp[s - 1] * pow2f(m - se[s - 1]) +
+                     ss[s + 1] * sp[s + 1] * pow2f(m - se[s + 1])) +
+          hx * hz * (ss[s - T::HX] * sp[s - T::HX] * pow2f(m - se[s - T::HX]) +
+                     ss[s + T::HX] * sp[s + T::HX] * pow2f(m - se[s + T::HX])) +
+          hx * hy * (ss[s - PL] * sp[s - PL] * pow2f(m - se[s - PL]) +
+                     ss[s + PL] * sp[s + PL] * pow2f(m - se[s + PL]));
+  }
+  return fmaf(-ss[s], acc, sp[s] * pow2f(m - ei));
+}
+
+// Pass 1: <ptil, Ahat ptil>; the last block forms alpha.
+template <int DIM>
+__global__ void __launch_bounds__(kThreads)
+k_mixed_pass1(Grid g, TileCount tc, const float *__restrict__ r32,
+              const float *__restrict__ p32, const short *__restrict__ e16,
+              const float *__restrict__ s32, MixState *st, double *part, int nblk_part) {
+  using T = Tile<DIM>;
+  constexpr int HN = T::HX * T::HY * T::HZ;
+  constexpr int TN = T::TX * T::TY * T::TZ;
+  __shared__ float sp[HN];
+  __shared__ int se[HN];
+  __shared__ float ss[HN];
+  __shared__ double shm[32];
+  __shared__ int shs[32];
+  __shared__ int flag;
+  if (st->done) return;
+  const float beta = (float)st->beta;
+  Acc32 acc{0.f, 0};
+  for (int64_t t = blockIdx.x; t < tc.total; t += gridDim.x) {
+    int x0, y0, z0;
+    tile_origin_m<DIM>(tc, t, x0, y0, z0);
+    stage_p<DIM>(g, x0, y0, z0, beta, r32, p32, e16, s32, sp, se, ss);
+    __syncthreads();
+    for (int lin = threadIdx.x; lin < TN; lin += blockDim.x) {
+      const int lx = lin % T::TX, ly = (lin / T::TX) % T::TY, lz = lin / (T::TX * T::TY);
+      const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
+      if (gx >= g.nx || gy >= g.ny || gz >= g.nz) continue;
+      const int s = (DIM == 3 ? (lz + 1) * T::HX * T::HY : 0) + (ly + 1) * T::HX + lx + 1;
+      if (sp[s] == 0.f) continue;
+      int E;
+      const float q = stencil_q<DIM>(g, sp, se, ss, s, gx, gy, gz, E);
+      // phat*qhat = ptil 2^-e * q 2^-E
+      acc_add(acc, sp[s] * q, -(se[s] + E));
+    }
+    __syncthreads();
+  }
+  const Acc64 tot = block_acc(to64(acc), shm, shs);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = tot.m;
+    part[nblk_part + blockIdx.x] = (double)tot.s;
+  }
+  if (!last_block(&st->counter[1], &flag)) return;
+  const Acc64 pq = sum_acc_partials(part, part + nblk_part, gridDim.x, shm, shs);
+  if (threadIdx.x == 0) {
+    const Acc64 rho{st->rho_m, st->rho_s};
+    if (pq.m > 0.0 && isfinite(pq.m)) {
+      st->alpha = acc_ratio(rho, pq);
+    } else if (rho.m == 0.0) {
+      st->alpha = 0.0;
+      st->done = 1;
+      st->status = EIK_OK;
+    } else {
+      st->alpha = 0.0;
+      st->done = 1;
+      st->status = EIK_ERR_BREAKDOWN;
+    }
+    st->counter[1] = 0u;
+  }
+}
+
+// Pass 2: d += alpha ptil (kx units), r -= alpha q, renormalise (r, p) per
+// node, write buffer set B; reduce <rhat, rhat> and the scaled residual max.
+template <int DIM>
+__global__ void __launch_bounds__(kThreads)
+k_mixed_pass2(Grid g, TileCount tc, CellGrid cg, const int *__restrict__ kx,
+              const float *__restrict__ r32, const float *__restrict__ p32,
+              const short *__restrict__ e16, const float *__restrict__ s32,
+              float *__restrict__ r32o, float *__restrict__ p32o, short *__restrict__ e16o,
+              float *__restrict__ d32, MixState *st, double *part, int nblk_part) {
+  using T = Tile<DIM>;
+  constexpr int HN = T::HX * T::HY * T::HZ;
+  constexpr int TN = T::TX * T::TY * T::TZ;
+  __shared__ float sp[HN];
+  __shared__ int se[HN];
+  __shared__ float ss[HN];
+  __shared__ double shm[32];
+  __shared__ int shs[32];
+  __shared__ float shf[32];
+  __shared__ int flag;
+  if (st->done) return;
+  const float beta = (float)st->beta, alpha = (float)st->alpha;
+  Acc32 acc{0.f, 0};
+  float rmax = 0.f;
+  for (int64_t t = blockIdx.x; t < tc.total; t += gridDim.x) {
+    int x0, y0, z0;
+    tile_origin_m<DIM>(tc, t, x0, y0, z0);
+    stage_p<DIM>(g, x0, y0, z0, beta, r32, p32, e16, s32, sp, se, ss);
+    __syncthreads();
+    for (int lin = threadIdx.x; lin < TN; lin += blockDim.x) {
+      const int lx = lin % T::TX, ly = (lin / T::TX) % T::TY, lz = lin / (T::TX * T::TY);
+      const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
+      if (gx >= g.nx || gy >= g.ny || gz >= g.nz) continue;
+      const int s = (DIM == 3 ? (lz + 1) * T::HX * T::HY : 0) + (ly + 1) * T::HX + lx + 1;
+      const int64_t gi = gx + (int64_t)g.nx * (gy + (int64_t)g.ny * gz);
+      const float pt = sp[s];
+      const int ei = se[s];
+      float rn = 0.f, pn = 0.f;
+      int en = kNoExp;
+      {
+        int E;
+        const float q = stencil_q<DIM>(g, sp, se, ss, s, gx, gy, gz, E);
+        const int ki = kx[cell_of(cg, gx, gy, gz)];
+        if (pt != 0.f) d32[gi] = fmaf(alpha * pt, pow2f(ki - ei), d32[gi]);
+        const float f = pow2f(E - ei);
+        const float rE = fmaf(-alpha, q, r32[gi] * f);   // r in E units
+        const float pE = pt * f;
+        const float mx = fmaxf(fabsf(rE), fabsf(pE));
+        if (mx > 0.f && isfinite(mx)) {
+          const int sh = expof(mx);
+          const float sc = pow2f(-sh);
+          rn = rE * sc;
+          pn = pE * sc;
+          en = E - sh;
+          acc_add(acc, rn * rn, -2 * en);
+          rmax = fmaxf(rmax, fabsf(rn) * pow2f(ki - en));
+        } else if (!isfinite(mx)) {
+          rmax = INFINITY;
+        }
+      }
+      r32o[gi] = rn;
+      p32o[gi] = pn;
+      e16o[gi] = (short)max(-32000, min(en, 32000));
+    }
+    __syncthreads();
+  }
+  const Acc64 tot = block_acc(to64(acc), shm, shs);
+  const float bm = block_maxf(rmax, shf);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = tot.m;
+    part[nblk_part + blockIdx.x] = (double)tot.s;
+    part[2 * nblk_part + blockIdx.x] = (double)bm;
+  }
+  if (!last_block(&st->counter[2], &flag)) return;
+  const Acc64 rr = sum_acc_partials(part, part + nblk_part, gridDim.x, shm, shs);
+  const double rm = max_partials(part + 2 * nblk_part, gridDim.x, shm);
+  if (threadIdx.x == 0) {
+    const Acc64 rho{st->rho_m, st->rho_s};
+    st->beta = acc_ratio(rr, rho);
+    st->rho_m = rr.m;
+    st->rho_s = rr.s;
+    st->iter += 1;
+    st->total_iter += 1;
+    if (!isfinite(rr.m) || !isfinite(st->beta)) {
+      st->done = 1;
+      st->status = EIK_ERR_BREAKDOWN;
+    } else if (rm <= (double)st->thresh || rr.m == 0.0) {
+      st->done = 1;
+      st->status = EIK_OK;
+    } else if (st->iter >= st->max_iter) {
+      st->done = 1;
+      st->status = EIK_ERR_NOT_CONVERGED;
+    }
+    st->counter[2] = 0u;
+  }
+}
+
+// x64 += d (kx units, unknowns only: d is zero on the sources).
+__global__ void k_mixed_update(int64_t n, const float *__restrict__ d32,
+                               double *__restrict__ x64) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float d = d32[i];
+    if (d != 0.f) x64[i] += (double)d;
+  }
+}
+
+// S = U_min - hbar log(phi'), phi' = sig xbar 2^-kx / sqrt(c) (Eq. SfromPhi);
+// sources are overwritten with U afterwards.
+__global__ void k_mixed_epilogue(Grid g, CellGrid cg, const int *__restrict__ kx,
+                                 const double *__restrict__ sig,
+                                 const double *__restrict__ x64, double *__restrict__ S,
+                                 double *__restrict__ phi) {
+  const double ln2 = 0.69314718055994530942;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % g.nx), y = (int)((i / g.nx) % g.ny);
+    const int z = (int)(i / ((int64_t)g.nx * g.ny));
+    const int kk = kx[cell_of(cg, x, y, z)];
+    const double si = sig[i], xi = x64[i];
+    const double v = ((si == 0.0) ? xi : si * xi) / g.sqrt_c;   // phi' 2^kx
+    const double Sv = g.U_min - g.hbar * (log(v) - kk * ln2);
+    S[i] = Sv;
+    if (phi) phi[i] = exp(-(Sv - g.U_min) / g.hbar);
+  }
+}
+
+}  // namespace
+
+// ====================================================================== host
+struct MixedState {
+  Grid g;
+  TileCount tc;
+  CellGrid cg;
+  int nblk_stencil = 0, nblk_part = 0, cap = 0;
+  float *s32 = nullptr, *fb = nullptr, *St = nullptr, *d32 = nullptr;
+  float *r32[2] = {nullptr, nullptr}, *p32[2] = {nullptr, nullptr};
+  short *e16[2] = {nullptr, nullptr};
+  int *kx = nullptr;
+  double *x64 = nullptr, *part = nullptr;
+  MixState *st = nullptr, *h_st = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int64_t launches[8] = {0};
+};
+
+static const char *kMixedNames[] = {"mixed_setup", "coarse_exponents", "mixed_residual64",
+                                    "mixed_pass1", "mixed_pass2", "mixed_update",
+                                    "mixed_epilogue", nullptr};
+
+const char *mixed_kernel_name(int k) {
+  if (k < 0 || k >= 7) return nullptr;
+  return kMixedNames[k];
+}
+
+int64_t mixed_kernel_launches(const MixedState *m, int k) {
+  return (m && k >= 0 && k < 8) ? m->launches[k] : 0;
+}
+
+void mixed_reset_launches(MixedState *m) {
+  if (m)
+    for (auto &v : m->launches) v = 0;
+}
+
+const char *mixed_last_error() { return g_msg.c_str(); }
+
+#define MCK(call)                                                        \
+  do {                                                                   \
+    cudaError_t e_ = (call);                                             \
+    if (e_ != cudaSuccess) {                                             \
+      g_msg = std::string(#call) + ": " + cudaGetErrorString(e_);        \
+      return EIK_ERR_CUDA;                                               \
+    }                                                                    \
+  } while (0)
+
+template <class T>
+static bool mal(T **p, size_t n) {
+  return cudaMalloc((void **)p, sizeof(T) * (n ? n : 1)) == cudaSuccess;
+}
+
+eik_status mixed_create(MixedState **out, const Grid &g, const TileCount &tc, int num_sms,
+                        cudaStream_t s) {
+  MixedState *m = new MixedState();
+  m->g = g;
+  m->tc = tc;
+  // cell edge: power of two >= 16 with at most kMaxCells cells
+  int lg = 4;
+  for (;; ++lg) {
+    const int B = 1 << lg;
+    const int64_t cx = (g.nx + B - 1) / B, cy = (g.ny + B - 1) / B;
+    const int64_t cz = (g.ndim == 3) ? (g.nz + B - 1) / B : 1;
+    if (cx * cy * cz <= kMaxCells) {
+      m->cg.B = B;
+      m->cg.lgB = lg;
+      m->cg.cx = (int)cx;
+      m->cg.cy = (int)cy;
+      m->cg.cz = (int)cz;
+      m->cg.ncell = (int)(cx * cy * cz);
+      break;
+    }
+  }
+  int per_sm = 0;
+  if (g.ndim == 2)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mixed_pass2<2>, kThreads, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mixed_pass2<3>, kThreads, 0);
+  if (per_sm < 1) per_sm = 1;
+  m->nblk_stencil = (int)std::min<int64_t>(tc.total, (int64_t)per_sm * num_sms);
+  m->cap = num_sms * 8;
+  m->nblk_part = std::max(m->nblk_stencil, m->cap);
+  const int64_t n = g.n;
+  bool ok = mal(&m->s32, n) && mal(&m->d32, n) && mal(&m->r32[0], n) && mal(&m->r32[1], n) &&
+            mal(&m->p32[0], n) && mal(&m->p32[1], n) && mal(&m->e16[0], n) &&
+            mal(&m->e16[1], n) && mal(&m->x64, n) && mal(&m->fb, m->cg.ncell) &&
+            mal(&m->St, m->cg.ncell) && mal(&m->kx, m->cg.ncell) &&
+            mal(&m->part, 8 * (size_t)m->nblk_part) && mal(&m->st, 1);
+  if (ok) ok = cudaMallocHost((void **)&m->h_st, sizeof(MixState)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    mixed_destroy(m);
+    g_msg = "device allocation failed";
+    return EIK_ERR_OOM;
+  }
+  const size_t smem = 2 * sizeof(float) * m->cg.ncell;
+  if (cudaFuncSetAttribute(k_coarse_exponents, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    mixed_destroy(m);
+    g_msg = "cannot reserve shared memory for the coarse estimate";
+    return EIK_ERR_CUDA;
+  }
+  (void)s;
+  *out = m;
+  return EIK_OK;
+}
+
+void mixed_destroy(MixedState *m) {
+  if (!m) return;
+  if (m->graph) cudaGraphExecDestroy(m->graph);
+  void *ptrs[] = {m->s32, m->fb, m->St, m->d32, m->r32[0], m->r32[1], m->p32[0],
+                  m->p32[1], m->e16[0], m->e16[1], m->kx, m->x64, m->part, m->st};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  if (m->h_st) cudaFreeHost(m->h_st);
+  delete m;
+}
+
+static void launch_residual(MixedState *m, const MixedArgs &a) {
+  if (m->g.ndim == 2)
+    k_mixed_residual<2><<<m->nblk_stencil, kThreads, 0, a.stream>>>(
+        m->g, m->tc, m->cg, m->kx, a.sig, m->x64, m->r32[0], m->p32[0], m->e16[0], m->d32,
+        m->st, m->part, m->nblk_part);
+  else
+    k_mixed_residual<3><<<m->nblk_stencil, kThreads, 0, a.stream>>>(
+        m->g, m->tc, m->cg, m->kx, a.sig, m->x64, m->r32[0], m->p32[0], m->e16[0], m->d32,
+        m->st, m->part, m->nblk_part);
+  m->launches[2]++;
+}
+
+static void launch_iteration(MixedState *m, int set, cudaStream_t s) {
+  const int a = set, b = 1 - set;
+  double *p1 = m->part;
+  double *p2 = m->part + 3 * (size_t)m->nblk_part;
+  if (m->g.ndim == 2) {
+    k_mixed_pass1<2><<<m->nblk_stencil, kThreads, 0, s>>>(m->g, m->tc, m->r32[a], m->p32[a],
+                                                         m->e16[a], m->s32, m->st, p1,
+                                                         m->nblk_part);
+    k_mixed_pass2<2><<<m->nblk_stencil, kThreads, 0, s>>>(
+        m->g, m->tc, m->cg, m->kx, m->r32[a], m->p32[a], m->e16[a], m->s32, m->r32[b],
+        m->p32[b], m->e16[b], m->d32, m->st, p2, m->nblk_part);
+  } else {
+    k_mixed_pass1<3><<<m->nblk_stencil, kThreads, 0, s>>>(m->g, m->tc, m->r32[a], m->p32[a],
+                                                         m->e16[a], m->s32, m->st, p1,
+                                                         m->nblk_part);
+    k_mixed_pass2<3><<<m->nblk_stencil, kThreads, 0, s>>>(
+        m->g, m->tc, m->cg, m->kx, m->r32[a], m->p32[a], m->e16[a], m->s32, m->r32[b],
+        m->p32[b], m->e16[b], m->d32, m->st, p2, m->nblk_part);
+  }
+}
+
+static eik_status build_graph(MixedState *m, cudaStream_t s) {
+  if (m->graph) return EIK_OK;
+  cudaGraph_t graph;
+  MCK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  for (int k = 0; k < kInnerGraphIters; ++k) launch_iteration(m, k & 1, s);
+  MCK(cudaStreamEndCapture(s, &graph));
+  MCK(cudaGraphInstantiate(&m->graph, graph, 0));
+  MCK(cudaGraphDestroy(graph));
+  return EIK_OK;
+}
+
+eik_status mixed_solve(MixedState *m, const MixedArgs &a, int *inner_iters, int *outer_iters,
+                       double *res_cw, double *res_nw) {
+  const Grid &g = m->g;
+  cudaStream_t s = a.stream;
+  const int cap = m->cap;
+  auto blocks = [&](int64_t n) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, cap));
+  };
+  // setup: FP32 coefficients, cell means of f, coarse distance -> exponents
+  k_sig32<<<blocks(g.n), kThreads, 0, s>>>(g.n, a.sig, m->s32);
+  k_cell_mean<<<m->cg.ncell, kThreads, 0, s>>>(g, m->cg, a.f, m->fb);
+  const size_t smem = 2 * sizeof(float) * m->cg.ncell;
+  k_coarse_exponents<<<1, 1024, smem, s>>>(g, m->cg, g.hbar / g.sqrt_c, m->fb, a.src, a.U,
+                                           a.nsrc, m->kx, m->St);
+  MCK(cudaMemsetAsync(m->x64, 0, sizeof(double) * g.n, s));
+  k_init_x64<<<(int)((a.nsrc + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+      g, m->cg, m->kx, a.src, a.U, a.nsrc, m->x64);
+  m->launches[0] += 3;
+  m->launches[1] += 1;
+  MCK(cudaGetLastError());
+  eik_status gs = build_graph(m, s);
+  if (gs != EIK_OK) return gs;
+
+  const double tol = a.opt.tol;
+  const double red = (a.opt.inner_tol > 0) ? a.opt.inner_tol : 1e-5;
+  const int max_outer = (a.opt.max_outer > 0) ? a.opt.max_outer : 30;
+  int total = 0, outer = 0;
+  double best_cw = INFINITY;
+  int stall = 0;
+  eik_status result = EIK_ERR_NOT_CONVERGED;
+  for (;;) {
+    MixState init{};
+    *m->h_st = init;
+    MCK(cudaMemcpyAsync(m->st, m->h_st, sizeof(MixState), cudaMemcpyHostToDevice, s));
+    launch_residual(m, a);
+    MCK(cudaGetLastError());
+    MCK(cudaMemcpyAsync(m->h_st, m->st, sizeof(MixState), cudaMemcpyDeviceToHost, s));
+    MCK(cudaStreamSynchronize(s));
+    const double cw = m->h_st->cw;
+    *res_cw = cw;
+    *res_nw = 0.0;
+    if (cw <= tol || m->h_st->rho_m == 0.0) {
+      result = EIK_OK;
+      break;
+    }
+    if (outer >= max_outer || total >= a.opt.max_iter) break;
+    if (cw < best_cw * 0.5) {
+      best_cw = cw;
+      stall = 0;
+    } else if (outer > 1 && ++stall >= 3) {
+      g_msg = "mixed refinement stopped making progress";
+      break;
+    }
+    // inner solve on the correction
+    MixState st = *m->h_st;
+    st.iter = 0;
+    st.done = 0;
+    st.status = 0;
+    st.beta = 0.0;
+    st.max_iter = a.opt.max_iter - total;
+    st.thresh = (float)std::max(red * st.r_inf, 0.3 * tol * st.x_inf);
+    *m->h_st = st;
+    MCK(cudaMemcpyAsync(m->st, m->h_st, sizeof(MixState), cudaMemcpyHostToDevice, s));
+    for (;;) {
+      MCK(cudaGraphLaunch(m->graph, s));
+      m->launches[3] += kInnerGraphIters;
+      m->launches[4] += kInnerGraphIters;
+      MCK(cudaMemcpyAsync(m->h_st, m->st, sizeof(MixState), cudaMemcpyDeviceToHost, s));
+      MCK(cudaStreamSynchronize(s));
+      if (m->h_st->done) break;
+    }
+    total += m->h_st->iter;
+    ++outer;
+    if (m->h_st->status == EIK_ERR_BREAKDOWN) {
+      g_msg = "inner CG breakdown";
+      result = EIK_ERR_BREAKDOWN;
+      break;
+    }
+    k_mixed_update<<<blocks(g.n), kThreads, 0, s>>>(g.n, m->d32, m->x64);
+    m->launches[5]++;
+    MCK(cudaGetLastError());
+  }
+  *inner_iters = total;
+  *outer_iters = outer;
+  return result;
+}
+
+eik_status mixed_write_outputs(MixedState *m, const MixedArgs &a, double *S, double *phi) {
+  const Grid &g = m->g;
+  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((g.n + kThreads - 1) / kThreads, m->cap));
+  k_mixed_epilogue<<<nb, kThreads, 0, a.stream>>>(g, m->cg, m->kx, a.sig, m->x64, S, phi);
+  m->launches[6]++;
+  MCK(cudaGetLastError());
+  return EIK_OK;
+}
 
 }  // namespace eik

@@ -32,7 +32,13 @@ eik_status mixed_create(MixedState **out, const Grid &g, const TileCount &tc, in
                         cudaStream_t s);
 eik_status mixed_solve(MixedState *m, const MixedArgs &a, int *inner_iters, int *outer_iters,
                        double *res_cw, double *res_nw);
+// Writes S (and phi if non-null) from the refined iterate; device pointers.
+eik_status mixed_write_outputs(MixedState *m, const MixedArgs &a, double *S, double *phi);
 void mixed_destroy(MixedState *m);
+int64_t mixed_kernel_launches(const MixedState *m, int k);
+void mixed_reset_launches(MixedState *m);
 const char *mixed_last_error();
+// Name of mixed-mode kernel k (0-based), or NULL past the last one.
+const char *mixed_kernel_name(int k);
 
 }  // namespace eik

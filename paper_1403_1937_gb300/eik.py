@@ -176,6 +176,29 @@ def eik_grad(handle: Handle, dLdS, dLdf_out=None):
     return dLdf_out, stats.as_dict()
 
 
+def eik_set_profiling(handle: Handle, enable: bool = True) -> None:
+    """Enables per-launch CUDA-event timing of the library's kernels (C:
+    ``eik_set_profiling``); graph launches are replaced by timed launches."""
+    _lib.check(_lib.load().eik_set_profiling(handle.ptr, int(bool(enable))))
+
+
+def eik_kernel_stats(handle: Handle):
+    """Per-kernel launch counts and timed device milliseconds (C:
+    ``eik_kernel_stats``) as a dict name -> (launches, timed, total_ms)."""
+    lib = _lib.load()
+    cnt = ctypes.c_int()
+    _lib.check(lib.eik_kernel_stats(handle.ptr, None, 0, ctypes.byref(cnt)))
+    arr = (_lib.KernelStat * max(cnt.value, 1))()
+    _lib.check(lib.eik_kernel_stats(handle.ptr, ctypes.cast(arr, ctypes.c_void_p),
+                                    cnt.value, ctypes.byref(cnt)))
+    return {a.name.decode(): (int(a.launches), int(a.timed_launches), float(a.total_ms))
+            for a in arr[:cnt.value]}
+
+
+def eik_reset_kernel_stats(handle: Handle) -> None:
+    _lib.check(_lib.load().eik_reset_kernel_stats(handle.ptr))
+
+
 def eik_destroy(handle: Handle) -> None:
     """Releases the handle (C: ``eik_destroy``); safe to call twice."""
     if handle is not None and handle._ptr:

@@ -1,0 +1,119 @@
+"""Mixed-precision path (FP32 block-floating-point inner CG + FP64 iterative
+refinement) vs the CPU oracle, through the C ABI.
+
+Bar (the benchmark spec): S absolute error <= 1e-6 against the FP64 oracle, on every
+config, including problems whose phi underflows float64 (S/hbar > 700), where
+the oracle uses its relative-form direct solve.
+"""
+import numpy as np
+import pytest
+
+from oracle import cg, fd
+from paper_1403_1937_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+S_ABS = 1e-6
+
+
+@pytest.fixture(scope="module")
+def eik():
+    import torch
+    from paper_1403_1937_gb300 import build
+    build.build()
+    from paper_1403_1937_gb300 import eik as e
+    assert torch.cuda.is_available()
+    return e
+
+
+def mixed_solve(eik, inst, tol=1e-9, boundary="half_cell", want_phi=False):
+    import torch
+    opt = eik.make_options(precision="mixed", tol=tol, boundary=boundary)
+    f = torch.from_numpy(np.ascontiguousarray(inst.f)).cuda()
+    h = eik.eik_create(inst.dims, inst.h, inst.hbar, f, inst.src_idx, inst.src_U, opt)
+    S, phi, stats = eik.eik_solve(h, want_phi=want_phi)
+    kst = eik.eik_kernel_stats(h)
+    eik.eik_destroy(h)
+    return S.cpu().numpy().ravel(), (phi.cpu().numpy().ravel() if want_phi else None), stats, kst
+
+
+def test_c1_mixed(eik):
+    inst = wl.config1()
+    S, phi, stats, kst = mixed_solve(eik, inst, want_phi=True)
+    S_ref, phi_ref, _ = fd.solve(inst.f, inst.dims, inst.h, inst.hbar, inst.src_idx)
+    assert np.max(np.abs(S - S_ref)) <= S_ABS
+    assert S[inst.src_idx[0]] == 0.0
+    assert stats["res_cw"] <= 1e-9
+    assert kst["mixed_pass1"][0] > 0 and kst["mixed_pass2"][0] > 0
+    assert kst["cg_pass1_64"][0] == 0      # the FP64 CG did not run
+
+
+@pytest.mark.parametrize("seed,ndim,boundary,with_U", [
+    (0, 2, "half_cell", False), (1, 2, "drop_edge", True), (2, 3, "half_cell", False),
+    (3, 3, "half_cell", True), (4, 2, "half_cell", False),
+])
+def test_random_ragged_mixed(eik, seed, ndim, boundary, with_U):
+    inst = wl.random_small(600 + seed, ndim=ndim, max_side=150 if ndim == 2 else 40,
+                           min_side=3, nsrc_max=6, with_U=with_U, hbar_over_h=(1.0, 6.0))
+    S, _, _, _ = mixed_solve(eik, inst, boundary=boundary)
+    S_ref, _, sys = fd.solve(inst.f, inst.dims, inst.h, inst.hbar, inst.src_idx, inst.src_U,
+                             boundary=1 if boundary == "drop_edge" else 0)
+    assert np.max(np.abs(S - S_ref)) <= S_ABS
+    assert np.array_equal(S[sys.src], sys.U)
+
+
+def test_c2_reduced_mixed(eik):
+    inst = wl.config2(n=512)
+    S, _, stats, _ = mixed_solve(eik, inst)
+    S_ref, _, _ = fd.solve(inst.f, inst.dims, inst.h, inst.hbar, inst.src_idx)
+    assert np.max(np.abs(S - S_ref)) <= S_ABS
+
+
+def test_c3_reduced_mixed(eik):
+    inst = wl.config3(n=48)
+    S, _, _, _ = mixed_solve(eik, inst)
+    S_ref, _, _, info = cg.solve(inst.f, inst.dims, inst.h, inst.hbar, inst.src_idx, tol=1e-13)
+    assert np.max(np.abs(S - S_ref)) <= S_ABS
+
+
+@pytest.mark.parametrize("n,mult,corner", [(400, 2, True), (300, 2, False)])
+def test_underflowing_phi(eik, n, mult, corner):
+    """hbar = 2h with f up to 1.5: S/hbar reaches several hundred, phi
+    underflows FP32 everywhere and FP64 in the far corner; the oracle solves
+    the diagonally similar relative form."""
+    rng = np.random.default_rng(n + mult)
+    dims = (n, n)
+    h = 1.0 / (n - 1)
+    f = wl.fourier_field(rng, dims, h)
+    src = np.array([0 if corner else n * (n // 2) + n // 2], dtype=np.int64)
+    inst = wl.Instance(dims, h, mult * h, f, src, np.zeros(1))
+    S, _, stats, _ = mixed_solve(eik, inst)
+    sys = fd.assemble(inst.f, inst.dims, inst.h, inst.hbar, inst.src_idx)
+    S_ref = fd.solve_relative(sys)
+    assert np.max(S_ref) / inst.hbar > 300
+    assert np.max(np.abs(S - S_ref)) <= S_ABS
+
+
+@pytest.mark.slow
+def test_c2_full_size_mixed(eik):
+    """Config 2 at 2048^2 in the bench's configuration (tol 1e-8)."""
+    inst = wl.config2()
+    S, _, stats, _ = mixed_solve(eik, inst, tol=1e-8)
+    S_ref, _, _, info = cg.solve(inst.f, inst.dims, inst.h, inst.hbar, inst.src_idx,
+                                 tol=1e-13)
+    assert info["status"] == 0
+    assert np.max(np.abs(S - S_ref)) <= S_ABS
+
+
+def test_fp64_at_bench_tolerance(eik):
+    """The plain FP64 path at the bench tolerance (1e-8) also meets S <= 1e-6
+    (reduced size, direct oracle)."""
+    import torch
+    inst = wl.config2(n=768)
+    opt = eik.make_options(precision="fp64", tol=1e-8)
+    f = torch.from_numpy(inst.f).cuda()
+    h = eik.eik_create(inst.dims, inst.h, inst.hbar, f, inst.src_idx, None, opt)
+    S, _, _ = eik.eik_solve(h)
+    eik.eik_destroy(h)
+    S_ref, _, _ = fd.solve(inst.f, inst.dims, inst.h, inst.hbar, inst.src_idx)
+    assert np.max(np.abs(S.cpu().numpy().ravel() - S_ref)) <= S_ABS
