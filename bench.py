@@ -39,6 +39,8 @@ UNIT = "GLUPS"
 ALGO_BYTES_PER_NODE = {
     "cg_pass1_64": 32,   # read r, p, sig; write q            (4 x 8 B)
     "cg_pass2_64": 56,   # read x, r, p, q; write x, r, p     (7 x 8 B)
+    "mixed_pass1": 14,   # read r, p (f32), e (i16), sig (f32)
+    "mixed_pass2": 32,   # read r, p, e, sig, d; write r, p, e (other set), d
 }
 
 
@@ -50,7 +52,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--workload", default="c2", choices=["c2", "c3"])
-    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=0,
@@ -89,13 +91,12 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+def kernel_source_hash(files):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1403_1937_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as fh:
-                h.update(fh.read())
+    for name in files:
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -108,7 +109,7 @@ def ncu_traffic(kernel, workload_name):
     with open(p) as fh:
         d = json.load(fh)
     e = d.get(f"{kernel}@{workload_name}")
-    if not e or e.get("source_sha") != kernel_source_hash():
+    if not e or e.get("source_sha") != kernel_source_hash(e.get("source_files", [])):
         return None
     return e.get("dram_bytes_per_launch")
 

@@ -154,6 +154,36 @@ eik_status eik_solve(eik_handle *h, double *S_out, double *phi_out,
 eik_status eik_grad(eik_handle *h, const double *dLdS, double *dLdf,
                     eik_stats *stats);
 
+/*
+ * Batched solves: many independent instances (own grid, h, hbar, f and
+ * sources; Sec. 6 system per instance) solved together.  Each instance runs
+ * on its own internal stream with its own convergence test, so the GPU
+ * executes the kernels of many instances concurrently; instances stop
+ * independently.  All instances share ndim and the options.
+ *   count        number of instances (>= 1)
+ *   dims         count*ndim extents, instance-major
+ *   h, hbar      count values each
+ *   f            sum_i N_i values, instances concatenated in order
+ *   src_offsets  count+1 offsets into src_idx / src_U (src_offsets[0] = 0)
+ *   src_idx      flat node indices within each instance's grid
+ *   src_U        values or NULL for zeros
+ * Outputs of eik_solve_batch / eik_grad_batch are concatenated the same way;
+ * stats (nullable) receives count entries.  The first failing instance's
+ * status is returned (all instances are still attempted).
+ */
+typedef struct eik_batch eik_batch;
+eik_status eik_create_batch(eik_batch **out, int count, int ndim, const int64_t *dims,
+                            const double *h, const double *hbar, const double *f,
+                            const int64_t *src_offsets, const int64_t *src_idx,
+                            const double *src_U, const eik_options *opt,
+                            eik_stream_t stream);
+eik_status eik_set_f_batch(eik_batch *b, const double *f);
+eik_status eik_solve_batch(eik_batch *b, double *S_out, eik_stats *stats);
+eik_status eik_grad_batch(eik_batch *b, const double *dLdS, double *dLdf, eik_stats *stats);
+eik_status eik_destroy_batch(eik_batch *b);
+/* Instances solved concurrently (host worker threads); 0 = library choice. */
+eik_status eik_batch_set_concurrency(eik_batch *b, int workers);
+
 /* Per-kernel counters of a handle (diagnostics; the paper has no
  * counterpart).  launches counts every kernel launch the handle issued since
  * creation or the last eik_reset_kernel_stats (kernels inside captured graphs

@@ -78,6 +78,15 @@ _SIGS = [
     ("eik_set_profiling", ctypes.c_int, [_P, ctypes.c_int]),
     ("eik_kernel_stats", ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     ("eik_reset_kernel_stats", ctypes.c_int, [_P]),
+    ("eik_create_batch", ctypes.c_int,
+     [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _P, _P, _P, _P,
+      ctypes.POINTER(Options), _P]),
+    ("eik_set_f_batch", ctypes.c_int, [_P, _P]),
+    ("eik_solve_batch", ctypes.c_int, [_P, _P, _P]),
+    ("eik_grad_batch", ctypes.c_int, [_P, _P, _P, _P]),
+    ("eik_destroy_batch", ctypes.c_int, [_P]),
+    ("eik_batch_set_concurrency", ctypes.c_int, [_P, ctypes.c_int]),
     ("eik_last_error", ctypes.c_char_p, []),
     ("eik_abi_version", ctypes.c_int, []),
     ("eik_cuda_arch", ctypes.c_int, []),

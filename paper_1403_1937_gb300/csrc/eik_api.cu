@@ -2,7 +2,10 @@
 // memory, stream ordering, the CG driver loop (captured in a CUDA graph),
 // restarts from the true residual, epilogue and adjoint.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <mutex>
+#include <thread>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -47,7 +50,7 @@ bool is_device_pointer(const void *p) {
 }
 
 constexpr int kGraphIters = 32;     // CG iterations per graph launch
-constexpr int kMaxRestarts = 4;     // restarts from the true residual
+constexpr int kMaxRestarts = 3;     // restarts in a row without progress
 
 // Kernels counted per handle (eik_kernel_stats).
 enum KernelId {
@@ -245,6 +248,8 @@ eik_status run_cg64(eik_handle *h, double *xs, const double *rhs, const double *
   init.stop_norm = stop_norm;
   *iters = 0;
   eik_status status = EIK_OK;
+  double last_res = INFINITY;
+  int stalled = 0;
   for (int restart = 0;; ++restart) {
     init.iter = *iters;
     *h->h_st = init;
@@ -269,8 +274,16 @@ eik_status run_cg64(eik_handle *h, double *xs, const double *rhs, const double *
     *res_nw = (h->h_st->res_nw2_b > 0) ? std::sqrt(h->h_st->res_nw2_r / h->h_st->res_nw2_b)
                                        : std::sqrt(h->h_st->res_nw2_r);
     if (ok_now || h->h_st->rho == 0.0) return EIK_OK;
-    if (*iters >= max_iter) return EIK_ERR_NOT_CONVERGED;
-    if (restart > kMaxRestarts) return status == EIK_OK ? EIK_ERR_NOT_CONVERGED : status;
+    if (*iters >= max_iter) return fail(EIK_ERR_NOT_CONVERGED, "maximum number of CG iterations reached");
+    // restarts continue while each one at least halves the true residual
+    const double now = (stop_norm == EIK_STOP_NORMWISE || weight) ? h->h_st->rho : h->h_st->res_cw;
+    if (restart > 0 && !(now < 0.5 * last_res)) {
+      if (++stalled >= kMaxRestarts)
+        return fail(EIK_ERR_NOT_CONVERGED, "restarts from the true residual stopped making progress");
+    } else {
+      stalled = 0;
+    }
+    last_res = std::min(last_res, now);
     cudaGraphExec_t exec = h->profiling ? nullptr : graph_for(h, xs, weight);
     for (;;) {
       if (exec) {
@@ -592,6 +605,9 @@ eik_status eik_solve(eik_handle *h, double *S_out, double *phi_out, eik_stats *s
     }
     if (s == EIK_OK || s == EIK_ERR_NOT_CONVERGED)
       write_outputs(h, S_out, phi_out, mixed ? &ma : nullptr);
+    // the adjoint works on the hat-space FP64 solution in h->x
+    if (mixed && s == EIK_OK && mixed_export_hat(h->mixed, ma, h->x) != EIK_OK)
+      throw CudaError{cudaErrorUnknown, "mixed export"};
     CK(cudaEventRecord(h->ev_t1, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     flush_timed(h);
@@ -686,6 +702,7 @@ eik_status eik_grad(eik_handle *h, const double *dLdS, double *dLdf, eik_stats *
 eik_status eik_set_profiling(eik_handle *h, int enable) {
   if (!h) return fail(EIK_ERR_ARG, "NULL handle");
   h->profiling = enable != 0;
+  mixed_set_profiling(h->mixed, h->profiling);
   return EIK_OK;
 }
 
@@ -702,6 +719,13 @@ eik_status eik_kernel_stats(eik_handle *h, eik_kernel_stat *out, int max, int *c
                         (id >= K_MIXED_FIRST ? mixed_kernel_launches(h->mixed, id - K_MIXED_FIRST) : 0);
       out[n].timed_launches = h->kstat[id].timed;
       out[n].total_ms = h->kstat[id].ms;
+      if (id >= K_MIXED_FIRST) {
+        int64_t t = 0;
+        double ms = 0.0;
+        mixed_kernel_time(h->mixed, id - K_MIXED_FIRST, &t, &ms);
+        out[n].timed_launches += t;
+        out[n].total_ms += ms;
+      }
     }
     ++n;
   }
@@ -718,6 +742,135 @@ eik_status eik_reset_kernel_stats(eik_handle *h) {
 
 eik_status eik_destroy(eik_handle *h) {
   free_handle(h);
+  return EIK_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batch
+struct eik_batch {
+  int count = 0;
+  int ndim = 2;
+  int workers = 0;
+  std::vector<eik_handle *> hs;
+  std::vector<int64_t> off;   // node offsets, count+1
+};
+
+namespace {
+
+// Runs fn(i) for every instance on a pool of host threads; each thread keeps
+// its own CUDA calls on the instance's internal stream.  Returns the first
+// non-OK status (by instance order) and its message.
+template <class F>
+eik_status run_pool(eik_batch *b, F fn) {
+  const int n = b->count;
+  int workers = b->workers > 0 ? b->workers : 16;
+  workers = std::max(1, std::min(workers, n));
+  std::vector<eik_status> st(n, EIK_OK);
+  std::vector<std::string> msg(n);
+  std::atomic<int> next{0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  auto work = [&]() {
+    cudaSetDevice(dev);
+    for (;;) {
+      const int i = next.fetch_add(1);
+      if (i >= n) break;
+      st[i] = fn(i);
+      if (st[i] != EIK_OK) msg[i] = eik_last_error();
+    }
+  };
+  std::vector<std::thread> th;
+  for (int w = 1; w < workers; ++w) th.emplace_back(work);
+  work();
+  for (auto &t : th) t.join();
+  for (int i = 0; i < n; ++i)
+    if (st[i] != EIK_OK) {
+      g_last_error = "instance " + std::to_string(i) + ": " + msg[i];
+      return st[i];
+    }
+  return EIK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+eik_status eik_create_batch(eik_batch **out, int count, int ndim, const int64_t *dims,
+                            const double *h, const double *hbar, const double *f,
+                            const int64_t *src_offsets, const int64_t *src_idx,
+                            const double *src_U, const eik_options *opt,
+                            eik_stream_t stream) {
+  if (!out) return fail(EIK_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (count < 1 || (ndim != 2 && ndim != 3) || !dims || !h || !hbar || !f || !src_offsets ||
+      !src_idx)
+    return fail(EIK_ERR_ARG, "invalid batch arguments");
+  eik_batch *b = new (std::nothrow) eik_batch();
+  if (!b) return fail(EIK_ERR_OOM, "host allocation failed");
+  b->count = count;
+  b->ndim = ndim;
+  b->off.assign(count + 1, 0);
+  std::vector<int64_t> so(count + 1);
+  if (cudaMemcpy(so.data(), src_offsets, sizeof(int64_t) * (count + 1), cudaMemcpyDefault) !=
+      cudaSuccess) {
+    delete b;
+    return fail(EIK_ERR_ARG, "cannot read src_offsets");
+  }
+  for (int i = 0; i < count; ++i) {
+    int64_t n = 1;
+    for (int a = 0; a < ndim; ++a) n *= dims[(int64_t)i * ndim + a];
+    b->off[i + 1] = b->off[i] + n;
+    if (so[i + 1] < so[i]) {
+      delete b;
+      return fail(EIK_ERR_ARG, "src_offsets must be non-decreasing");
+    }
+  }
+  b->hs.assign(count, nullptr);
+  for (int i = 0; i < count; ++i) {
+    eik_status st = eik_create(&b->hs[i], ndim, dims + (int64_t)i * ndim, h[i], hbar[i],
+                               f + b->off[i], src_idx + so[i], src_U ? src_U + so[i] : nullptr,
+                               so[i + 1] - so[i], opt, stream);
+    if (st != EIK_OK) {
+      const std::string m = "instance " + std::to_string(i) + ": " + g_last_error;
+      eik_destroy_batch(b);
+      return fail(st, m);
+    }
+  }
+  *out = b;
+  return EIK_OK;
+}
+
+eik_status eik_batch_set_concurrency(eik_batch *b, int workers) {
+  if (!b) return fail(EIK_ERR_ARG, "NULL batch");
+  b->workers = workers;
+  return EIK_OK;
+}
+
+eik_status eik_set_f_batch(eik_batch *b, const double *f) {
+  if (!b || !f) return fail(EIK_ERR_ARG, "NULL batch or f");
+  return run_pool(b, [&](int i) { return eik_set_f(b->hs[i], f + b->off[i]); });
+}
+
+eik_status eik_solve_batch(eik_batch *b, double *S_out, eik_stats *stats) {
+  if (!b || !S_out) return fail(EIK_ERR_ARG, "NULL batch or S_out");
+  return run_pool(b, [&](int i) {
+    return eik_solve(b->hs[i], S_out + b->off[i], nullptr, stats ? stats + i : nullptr);
+  });
+}
+
+eik_status eik_grad_batch(eik_batch *b, const double *dLdS, double *dLdf, eik_stats *stats) {
+  if (!b || !dLdS || !dLdf) return fail(EIK_ERR_ARG, "NULL batch, dLdS or dLdf");
+  return run_pool(b, [&](int i) {
+    return eik_grad(b->hs[i], dLdS + b->off[i], dLdf + b->off[i], stats ? stats + i : nullptr);
+  });
+}
+
+eik_status eik_destroy_batch(eik_batch *b) {
+  if (!b) return EIK_OK;
+  for (eik_handle *h : b->hs)
+    if (h) free_handle(h);
+  delete b;
   return EIK_OK;
 }
 

@@ -21,6 +21,8 @@
 
 namespace eik {
 
+constexpr int kCheckEvery = 4;   // iterations between componentwise tests
+
 // ------------------------------------------------------------------ setup
 __global__ void k_setup64(Grid g, const double *__restrict__ f,
                           double *__restrict__ sig, double *__restrict__ x,
@@ -89,6 +91,15 @@ __device__ __forceinline__ double nb_sum(const double *u, int s, const Grid &g,
     return hy * hz * (u[s - 1] + u[s + 1]) + hx * hz * (u[s - T::HX] + u[s + T::HX]) +
            hx * hy * (u[s - PL] + u[s + PL]);
   }
+}
+
+// Unweighted neighbour sum (no node of the tile lies on a face).
+template <int DIM>
+__device__ __forceinline__ double nb_sum_plain(const double *u, int s) {
+  using T = Tile<DIM>;
+  if (DIM == 2) return (u[s - 1] + u[s + 1]) + (u[s - T::HX] + u[s + T::HX]);
+  constexpr int PL = T::HX * T::HY;
+  return ((u[s - 1] + u[s + 1]) + (u[s - T::HX] + u[s + T::HX])) + (u[s - PL] + u[s + PL]);
 }
 
 // ---------------------------------------------------------- true residual
@@ -209,6 +220,10 @@ k_pass1_64(Grid g, TileCount tc, const double *__restrict__ sig,
   for (int64_t t = blockIdx.x; t < tc.total; t += gridDim.x) {
     int x0, y0, z0;
     tile_origin<DIM>(tc, t, x0, y0, z0);
+    // tiles that hold no face node need no face weights
+    const bool interior = x0 >= 1 && x0 + T::TX <= g.nx - 1 && y0 >= 1 &&
+                          y0 + T::TY <= g.ny - 1 &&
+                          (DIM == 2 || (z0 >= 1 && z0 + T::TZ <= g.nz - 1));
     for (int s = threadIdx.x; s < HN; s += blockDim.x) {
       const int hx = s % T::HX;
       const int hy = (s / T::HX) % T::HY;
@@ -234,7 +249,8 @@ k_pass1_64(Grid g, TileCount tc, const double *__restrict__ sig,
       const int s = (DIM == 3 ? (lz + 1) * T::HX * T::HY : 0) + (ly + 1) * T::HX + lx + 1;
       const int64_t gi = gx + (int64_t)g.nx * (gy + (int64_t)g.ny * gz);
       const double pt = sp[s];
-      const double qv = fma(-sig[gi], nb_sum<DIM>(su, s, g, gx, gy, gz), pt);
+      const double nb = interior ? nb_sum_plain<DIM>(su, s) : nb_sum<DIM>(su, s, g, gx, gy, gz);
+      const double qv = fma(-sig[gi], nb, pt);
       q[gi] = qv;
       acc = fma(pt, qv, acc);
     }
@@ -271,7 +287,10 @@ k_pass2_64(int64_t n, double *__restrict__ x, double *__restrict__ r,
   __shared__ int flag;
   if (st->done) return;
   const double alpha = st->alpha, beta = st->beta, tol = st->tol;
-  const bool cw_stop = (st->stop_norm == EIK_STOP_COMPONENTWISE);
+  // the componentwise test costs three FP64 operations per node, so it is
+  // evaluated on every kCheckEvery-th iteration only
+  const bool check = ((st->iter + 1) % kCheckEvery) == 0;
+  const bool cw_stop = (st->stop_norm == EIK_STOP_COMPONENTWISE) && check;
   double acc = 0.0, bad = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -305,8 +324,8 @@ k_pass2_64(int64_t n, double *__restrict__ x, double *__restrict__ r,
     st->rho = rr;
     st->iter += 1;
     bool conv;
-    if (cw_stop)
-      conv = (anybad == 0.0);
+    if (st->stop_norm == EIK_STOP_COMPONENTWISE)
+      conv = cw_stop && (anybad == 0.0);
     else
       conv = (rr <= st->tol * st->tol * st->bnorm2);
     if (!isfinite(rr)) {

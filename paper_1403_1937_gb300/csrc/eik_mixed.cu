@@ -26,7 +26,9 @@
 // form and solves for a correction with a fresh inner CG.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 
+#include <cmath>
 #include <string>
 
 #include "eik_launch.h"
@@ -43,10 +45,9 @@ constexpr int kMaxCells = 16384;
 std::string g_msg = "no error";
 
 // ------------------------------------------------------------ exponents
+// 2^n as a float; 0 below the normal range, 2^127 above it.
 __device__ __forceinline__ float pow2f(int n) {
-  if (n < -126) return 0.f;
-  if (n > 127) n = 127;
-  return __int_as_float((n + 127) << 23);
+  return __int_as_float(min(max(n + 127, 0), 254) << 23);
 }
 __device__ __forceinline__ double pow2d(int n) {
   if (n < -1022) return 0.0;
@@ -159,7 +160,9 @@ struct MixState {
   int rho_s;
   int iter;          // inner iterations of the current solve
   double alpha, beta;
-  float thresh;      // stop when max_i |rhat_i| 2^kx(i) <= thresh
+  float thresh;      // mode 0: stop when max_i |rhat_i| 2^kx(i) <= thresh
+  float theta;       // mode 1: stop when |rhat_i| 2^kx(i) <= theta |xref_i + d_i| for all i
+  int mode;
   int max_iter;
   int done;
   int status;
@@ -328,7 +331,8 @@ __global__ void __launch_bounds__(kThreads)
 k_mixed_residual(Grid g, TileCount tc, CellGrid cg, const int *__restrict__ kx,
                  const double *__restrict__ sig, const double *__restrict__ x64,
                  float *__restrict__ r32, float *__restrict__ p32, short *__restrict__ e16,
-                 float *__restrict__ d32, MixState *st, double *part, int nblk_part) {
+                 float *__restrict__ d32, float *__restrict__ xref, MixState *st, double *part,
+                 int nblk_part) {
   using T = Tile<DIM>;
   constexpr int HN = T::HX * T::HY * T::HZ;
   constexpr int TN = T::TX * T::TY * T::TZ;
@@ -402,6 +406,7 @@ k_mixed_residual(Grid g, TileCount tc, CellGrid cg, const int *__restrict__ kx,
       p32[gi] = 0.f;
       e16[gi] = (short)max(-32000, min(e, 32000));
       d32[gi] = 0.f;
+      xref[gi] = (si != 0.0) ? (float)xi : 0.f;
     }
     __syncthreads();
   }
@@ -457,40 +462,53 @@ __device__ __forceinline__ void stage_p(const Grid &g, int x0, int y0, int z0, f
     }
     sp[s] = pv;
     se[s] = ev;
-    ss[s] = sv;
+    ss[s] = sv * pv;   // u = sig * ptil
   }
 }
 
 // q in units of E = min exponent of the stencil (the largest scale), so no
-// term can overflow: q = ptil_i 2^(E-e_i) - sig_i sum_j omega sig_j ptil_j 2^(E-e_j).
+// term can overflow: q = ptil_i 2^(E-e_i) - sig_i sum_j omega u_j 2^(E-e_j),
+// u = sig * ptil (staged in su).  sig_i is passed by the caller.
 template <int DIM>
 __device__ __forceinline__ float stencil_q(const Grid &g, const float *sp, const int *se,
                                            const float *ss, int s, int gx, int gy, int gz,
-                                           int &E) {
+                                           float sig_i, bool interior, int &E) {
   using T = Tile<DIM>;
   constexpr int PL = T::HX * T::HY;
   const int ei = se[s];
   int m = min(ei, min(min(se[s - 1], se[s + 1]), min(se[s - T::HX], se[s + T::HX])));
   if (DIM == 3) m = min(m, min(se[s - PL], se[s + PL]));
   E = m;
-  const float hx = on_face(gx, g.nx, g.boundary) ? 0.5f : 1.f;
-  const float hy = on_face(gy, g.ny, g.boundary) ? 0.5f : 1.f;
+  const float a1 = ss[s - 1] * pow2f(m - se[s - 1]) + ss[s + 1] * pow2f(m - se[s + 1]);
+  const float a2 = ss[s - T::HX] * pow2f(m - se[s - T::HX]) + ss[s + T::HX] * pow2f(m - se[s + T::HX]);
   float acc;
   if (DIM == 2) {
-    acc = hy * (ss[s - 1] * sp[s - 1] * pow2f(m - se[s - 1]) +
-                ss[s + 1] * sp[s + 1] * pow2f(m - se[s + 1])) +
-          hx * (ss[s - T::HX] * sp[s - T::HX] * pow2f(m - se[s - T::HX]) +
-                ss[s + T::HX] * sp[s + T::HX] * pow2f(m - se[s + T::HX]));
+    if (interior) {
+      acc = a1 + a2;
+    } else {
+      const float hx = on_face(gx, g.nx, g.boundary) ? 0.5f : 1.f;
+      const float hy = on_face(gy, g.ny, g.boundary) ? 0.5f : 1.f;
+      acc = fmaf(hy, a1, hx * a2);
+    }
   } else {
-    const float hz = on_face(gz, g.nz, g.boundary) ? 0.5f : 1.f;
-    acc = hy * hz * (ss[s - 1] * sp[s - 1] * pow2f(m - se[s - 1]) +
-                     ss[s + 1] * sp[s + 1] * pow2f(m - se[s + 1])) +
-          hx * hz * (ss[s - T::HX] * sp[s - T::HX] * pow2f(m - se[s - T::HX]) +
-                     ss[s + T::HX] * sp[s + T::HX] * pow2f(m - se[s + T::HX])) +
-          hx * hy * (ss[s - PL] * sp[s - PL] * pow2f(m - se[s - PL]) +
-                     ss[s + PL] * sp[s + PL] * pow2f(m - se[s + PL]));
+    const float a3 = ss[s - PL] * pow2f(m - se[s - PL]) + ss[s + PL] * pow2f(m - se[s + PL]);
+    if (interior) {
+      acc = (a1 + a2) + a3;
+    } else {
+      const float hx = on_face(gx, g.nx, g.boundary) ? 0.5f : 1.f;
+      const float hy = on_face(gy, g.ny, g.boundary) ? 0.5f : 1.f;
+      const float hz = on_face(gz, g.nz, g.boundary) ? 0.5f : 1.f;
+      acc = hy * hz * a1 + hx * hz * a2 + hx * hy * a3;
+    }
   }
-  return fmaf(-ss[s], acc, sp[s] * pow2f(m - ei));
+  return fmaf(-sig_i, acc, sp[s] * pow2f(m - ei));
+}
+
+template <int DIM>
+__device__ __forceinline__ bool tile_interior(const Grid &g, int x0, int y0, int z0) {
+  using T = Tile<DIM>;
+  return x0 >= 1 && x0 + T::TX <= g.nx - 1 && y0 >= 1 && y0 + T::TY <= g.ny - 1 &&
+         (DIM == 2 || (z0 >= 1 && z0 + T::TZ <= g.nz - 1));
 }
 
 // Pass 1: <ptil, Ahat ptil>; the last block forms alpha.
@@ -515,6 +533,7 @@ k_mixed_pass1(Grid g, TileCount tc, const float *__restrict__ r32,
     int x0, y0, z0;
     tile_origin_m<DIM>(tc, t, x0, y0, z0);
     stage_p<DIM>(g, x0, y0, z0, beta, r32, p32, e16, s32, sp, se, ss);
+    const bool interior = tile_interior<DIM>(g, x0, y0, z0);
     __syncthreads();
     for (int lin = threadIdx.x; lin < TN; lin += blockDim.x) {
       const int lx = lin % T::TX, ly = (lin / T::TX) % T::TY, lz = lin / (T::TX * T::TY);
@@ -522,8 +541,9 @@ k_mixed_pass1(Grid g, TileCount tc, const float *__restrict__ r32,
       if (gx >= g.nx || gy >= g.ny || gz >= g.nz) continue;
       const int s = (DIM == 3 ? (lz + 1) * T::HX * T::HY : 0) + (ly + 1) * T::HX + lx + 1;
       if (sp[s] == 0.f) continue;
+      const int64_t gi = gx + (int64_t)g.nx * (gy + (int64_t)g.ny * gz);
       int E;
-      const float q = stencil_q<DIM>(g, sp, se, ss, s, gx, gy, gz, E);
+      const float q = stencil_q<DIM>(g, sp, se, ss, s, gx, gy, gz, s32[gi], interior, E);
       // phat*qhat = ptil 2^-e * q 2^-E
       acc_add(acc, sp[s] * q, -(se[s] + E));
     }
@@ -561,7 +581,8 @@ k_mixed_pass2(Grid g, TileCount tc, CellGrid cg, const int *__restrict__ kx,
               const float *__restrict__ r32, const float *__restrict__ p32,
               const short *__restrict__ e16, const float *__restrict__ s32,
               float *__restrict__ r32o, float *__restrict__ p32o, short *__restrict__ e16o,
-              float *__restrict__ d32, MixState *st, double *part, int nblk_part) {
+              float *__restrict__ d32, const float *__restrict__ xref, MixState *st,
+              double *part, int nblk_part) {
   using T = Tile<DIM>;
   constexpr int HN = T::HX * T::HY * T::HZ;
   constexpr int TN = T::TX * T::TY * T::TZ;
@@ -574,12 +595,15 @@ k_mixed_pass2(Grid g, TileCount tc, CellGrid cg, const int *__restrict__ kx,
   __shared__ int flag;
   if (st->done) return;
   const float beta = (float)st->beta, alpha = (float)st->alpha;
+  const int mode = st->mode;
+  const float theta = st->theta;
   Acc32 acc{0.f, 0};
   float rmax = 0.f;
   for (int64_t t = blockIdx.x; t < tc.total; t += gridDim.x) {
     int x0, y0, z0;
     tile_origin_m<DIM>(tc, t, x0, y0, z0);
     stage_p<DIM>(g, x0, y0, z0, beta, r32, p32, e16, s32, sp, se, ss);
+    const bool interior = tile_interior<DIM>(g, x0, y0, z0);
     __syncthreads();
     for (int lin = threadIdx.x; lin < TN; lin += blockDim.x) {
       const int lx = lin % T::TX, ly = (lin / T::TX) % T::TY, lz = lin / (T::TX * T::TY);
@@ -593,9 +617,13 @@ k_mixed_pass2(Grid g, TileCount tc, CellGrid cg, const int *__restrict__ kx,
       int en = kNoExp;
       {
         int E;
-        const float q = stencil_q<DIM>(g, sp, se, ss, s, gx, gy, gz, E);
+        const float q = stencil_q<DIM>(g, sp, se, ss, s, gx, gy, gz, s32[gi], interior, E);
         const int ki = kx[cell_of(cg, gx, gy, gz)];
-        if (pt != 0.f) d32[gi] = fmaf(alpha * pt, pow2f(ki - ei), d32[gi]);
+        float dn = d32[gi];
+        if (pt != 0.f) {
+          dn = fmaf(alpha * pt, pow2f(ki - ei), dn);
+          d32[gi] = dn;
+        }
         const float f = pow2f(E - ei);
         const float rE = fmaf(-alpha, q, r32[gi] * f);   // r in E units
         const float pE = pt * f;
@@ -607,7 +635,11 @@ k_mixed_pass2(Grid g, TileCount tc, CellGrid cg, const int *__restrict__ kx,
           pn = pE * sc;
           en = E - sh;
           acc_add(acc, rn * rn, -2 * en);
-          rmax = fmaxf(rmax, fabsf(rn) * pow2f(ki - en));
+          const float rk = fabsf(rn) * pow2f(ki - en);   // |rhat| in kx units
+          if (mode == 0)
+            rmax = fmaxf(rmax, rk);
+          else if (rk > theta * fabsf(xref[gi] + dn))
+            rmax = 1.f;                                   // not yet converged here
         } else if (!isfinite(mx)) {
           rmax = INFINITY;
         }
@@ -638,7 +670,7 @@ k_mixed_pass2(Grid g, TileCount tc, CellGrid cg, const int *__restrict__ kx,
     if (!isfinite(rr.m) || !isfinite(st->beta)) {
       st->done = 1;
       st->status = EIK_ERR_BREAKDOWN;
-    } else if (rm <= (double)st->thresh || rr.m == 0.0) {
+    } else if ((st->mode == 0 ? rm <= (double)st->thresh : rm == 0.0) || rr.m == 0.0) {
       st->done = 1;
       st->status = EIK_OK;
     } else if (st->iter >= st->max_iter) {
@@ -646,6 +678,255 @@ k_mixed_pass2(Grid g, TileCount tc, CellGrid cg, const int *__restrict__ kx,
       st->status = EIK_ERR_NOT_CONVERGED;
     }
     st->counter[2] = 0u;
+  }
+}
+
+// ------------------------------------------- 2D inner CG, warp-marched rows
+// Specialisation for 2D grids with nx % 4 == 0: a warp owns 128 consecutive
+// columns (4 per lane, float4 loads) and marches down kRowsPerWarp rows,
+// keeping the rows above and below in registers and taking the x neighbours
+// by warp shuffle (lanes 0 and 31 load the column beyond the warp).  No shared
+// memory and no block barrier on the data path; the next row's loads are
+// issued before the current row is computed.  Arithmetic is that of
+// stencil_q / k_mixed_pass1 / k_mixed_pass2 above.
+constexpr int kRowsPerWarp = 4;
+constexpr int kWarpsPerBlock = 8;
+constexpr int kRowTile = kRowsPerWarp * kWarpsPerBlock;   // rows per block tile
+
+struct Row {
+  float4 r, pt, s, u;
+  int e0, e1, e2, e3;
+  float uL, uR;
+  int eL, eR;
+};
+
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+
+__device__ __forceinline__ void load_row(const Grid &g, int x, int xw, int y, float beta,
+                                         const float *__restrict__ r32,
+                                         const float *__restrict__ p32,
+                                         const short *__restrict__ e16,
+                                         const float *__restrict__ s32, Row &R) {
+  const int lane = threadIdx.x & 31;
+  const bool in = (y >= 0) && (y < g.ny) && (x < g.nx);
+  if (in) {
+    const int64_t o = (int64_t)y * g.nx + x;
+    R.r = ld4(r32 + o);
+    const float4 p = ld4(p32 + o);
+    R.s = ld4(s32 + o);
+    const uint2 ev = *reinterpret_cast<const uint2 *>(e16 + o);
+    R.e0 = (short)(ev.x & 0xffff);
+    R.e1 = (short)(ev.x >> 16);
+    R.e2 = (short)(ev.y & 0xffff);
+    R.e3 = (short)(ev.y >> 16);
+    R.pt = make_float4(fmaf(beta, p.x, R.r.x), fmaf(beta, p.y, R.r.y), fmaf(beta, p.z, R.r.z),
+                       fmaf(beta, p.w, R.r.w));
+    R.u = make_float4(R.s.x * R.pt.x, R.s.y * R.pt.y, R.s.z * R.pt.z, R.s.w * R.pt.w);
+  } else {
+    R.r = R.pt = R.s = R.u = make_float4(0.f, 0.f, 0.f, 0.f);
+    R.e0 = R.e1 = R.e2 = R.e3 = kNoExp;
+  }
+  R.uL = __shfl_up_sync(0xffffffffu, R.u.w, 1);
+  R.eL = __shfl_up_sync(0xffffffffu, R.e3, 1);
+  R.uR = __shfl_down_sync(0xffffffffu, R.u.x, 1);
+  R.eR = __shfl_down_sync(0xffffffffu, R.e0, 1);
+  if (lane == 0 || lane == 31) {
+    const int xn = (lane == 0) ? xw - 1 : xw + 128;
+    float uu = 0.f;
+    int ee = kNoExp;
+    if (y >= 0 && y < g.ny && xn >= 0 && xn < g.nx) {
+      const int64_t o = (int64_t)y * g.nx + xn;
+      uu = s32[o] * fmaf(beta, p32[o], r32[o]);
+      ee = e16[o];
+    }
+    if (lane == 0) {
+      R.uL = uu;
+      R.eL = ee;
+    } else {
+      R.uR = uu;
+      R.eR = ee;
+    }
+  }
+}
+
+// q for column j of the current row (E returned); u/e of the x neighbours,
+// the row above (a) and below (b).
+__device__ __forceinline__ float q_node(float pt, float sg, int ei, float uL, int eL, float uR,
+                                        int eR, float ua, int ea, float ub, int eb, float hx,
+                                        float hy, int &E) {
+  const int m = min(min(ei, min(eL, eR)), min(ea, eb));
+  E = m;
+  const float a1 = uL * pow2f(m - eL) + uR * pow2f(m - eR);
+  const float a2 = ua * pow2f(m - ea) + ub * pow2f(m - eb);
+  return fmaf(-sg, fmaf(hy, a1, hx * a2), pt * pow2f(m - ei));
+}
+
+template <bool PASS2>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+k_mixed2d(Grid g, CellGrid cg, int tiles_x, int ntiles, const int *__restrict__ kx,
+          const float *__restrict__ r32, const float *__restrict__ p32,
+          const short *__restrict__ e16, const float *__restrict__ s32,
+          float *__restrict__ r32o, float *__restrict__ p32o, short *__restrict__ e16o,
+          float *__restrict__ d32, const float *__restrict__ xref, MixState *st, double *part,
+          int nblk_part) {
+  __shared__ double shm[32];
+  __shared__ int shs[32];
+  __shared__ float shf[32];
+  __shared__ int flag;
+  if (st->done) return;
+  const float beta = (float)st->beta, alpha = (float)st->alpha;
+  const int mode = st->mode;
+  const float theta = st->theta;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool half = g.boundary == EIK_BOUNDARY_HALF_CELL;
+  Acc32 acc{0.f, 0};
+  float rmax = 0.f;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int xw = (t % tiles_x) * 128;
+    const int x = xw + 4 * lane;
+    const int y0 = (t / tiles_x) * kRowTile + warp * kRowsPerWarp;
+    if (y0 >= g.ny) continue;   // whole warp: uniform
+    // face weights of the 4 columns (x edges carry hy, y edges hx)
+    const float hx0 = (half && (x == 0 || x == g.nx - 1)) ? 0.5f : 1.f;
+    const float hx1 = (half && (x + 1 == g.nx - 1)) ? 0.5f : 1.f;
+    const float hx2 = (half && (x + 2 == g.nx - 1)) ? 0.5f : 1.f;
+    const float hx3 = (half && (x + 3 == g.nx - 1)) ? 0.5f : 1.f;
+    Row A, C, B;   // above, current, below
+    load_row(g, x, xw, y0 - 1, beta, r32, p32, e16, s32, A);
+    load_row(g, x, xw, y0, beta, r32, p32, e16, s32, C);
+    for (int k = 0; k < kRowsPerWarp; ++k) {
+      const int y = y0 + k;
+      load_row(g, x, xw, y + 1, beta, r32, p32, e16, s32, B);
+      if (y < g.ny && x < g.nx) {
+        const float hy = (half && (y == 0 || y == g.ny - 1)) ? 0.5f : 1.f;
+        int E0, E1, E2, E3;
+        const float q0 = q_node(C.pt.x, C.s.x, C.e0, C.uL, C.eL, C.u.y, C.e1, A.u.x, A.e0, B.u.x,
+                                B.e0, hx0, hy, E0);
+        const float q1 = q_node(C.pt.y, C.s.y, C.e1, C.u.x, C.e0, C.u.z, C.e2, A.u.y, A.e1, B.u.y,
+                                B.e1, hx1, hy, E1);
+        const float q2 = q_node(C.pt.z, C.s.z, C.e2, C.u.y, C.e1, C.u.w, C.e3, A.u.z, A.e2, B.u.z,
+                                B.e2, hx2, hy, E2);
+        const float q3 = q_node(C.pt.w, C.s.w, C.e3, C.u.z, C.e2, C.uR, C.eR, A.u.w, A.e3, B.u.w,
+                                B.e3, hx3, hy, E3);
+        if (!PASS2) {
+          // <phat, qhat>: terms pt*q 2^-(e+E); align to the largest scale
+          const int t0 = -(C.e0 + E0), t1 = -(C.e1 + E1), t2 = -(C.e2 + E2), t3 = -(C.e3 + E3);
+          const int tm = max(max(t0, t1), max(t2, t3));
+          const float sum = C.pt.x * q0 * pow2f(t0 - tm) + C.pt.y * q1 * pow2f(t1 - tm) +
+                            C.pt.z * q2 * pow2f(t2 - tm) + C.pt.w * q3 * pow2f(t3 - tm);
+          acc_add(acc, sum, tm);
+        } else {
+          const int64_t o = (int64_t)y * g.nx + x;
+          const int ki = kx[(x >> cg.lgB) + cg.cx * (y >> cg.lgB)];
+          float4 d = ld4(d32 + o);
+          float rn[4], pn[4];
+          int en[4];
+          const float pts[4] = {C.pt.x, C.pt.y, C.pt.z, C.pt.w};
+          const float rs[4] = {C.r.x, C.r.y, C.r.z, C.r.w};
+          const float qs[4] = {q0, q1, q2, q3};
+          const int es[4] = {C.e0, C.e1, C.e2, C.e3};
+          const int Es[4] = {E0, E1, E2, E3};
+          float dd[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if (pts[j] != 0.f) dd[j] = fmaf(alpha * pts[j], pow2f(ki - es[j]), dd[j]);
+            const float f = pow2f(Es[j] - es[j]);
+            const float rE = fmaf(-alpha, qs[j], rs[j] * f);
+            const float pE = pts[j] * f;
+            const float mx = fmaxf(fabsf(rE), fabsf(pE));
+            if (mx > 0.f && mx <= 3.4e38f) {
+              const int sh = expof(mx);
+              const float sc = pow2f(-sh);
+              rn[j] = rE * sc;
+              pn[j] = pE * sc;
+              en[j] = Es[j] - sh;
+            } else {
+              rn[j] = 0.f;
+              pn[j] = 0.f;
+              en[j] = kNoExp;
+              if (!(mx <= 3.4e38f)) rmax = INFINITY;
+            }
+          }
+          // <rhat, rhat> terms rn^2 2^-2en
+          const int t0 = -2 * en[0], t1 = -2 * en[1], t2 = -2 * en[2], t3 = -2 * en[3];
+          const int tm = max(max(t0, t1), max(t2, t3));
+          const float sum = rn[0] * rn[0] * pow2f(t0 - tm) + rn[1] * rn[1] * pow2f(t1 - tm) +
+                            rn[2] * rn[2] * pow2f(t2 - tm) + rn[3] * rn[3] * pow2f(t3 - tm);
+          acc_add(acc, sum, tm);
+          float4 xr = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (mode != 0) xr = ld4(xref + o);
+          const float xrs[4] = {xr.x, xr.y, xr.z, xr.w};
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if (rn[j] == 0.f) continue;
+            const float rk = fabsf(rn[j]) * pow2f(ki - en[j]);
+            if (mode == 0)
+              rmax = fmaxf(rmax, rk);
+            else if (rk > theta * fabsf(xrs[j] + dd[j]))
+              rmax = 1.f;
+          }
+          *reinterpret_cast<float4 *>(d32 + o) = make_float4(dd[0], dd[1], dd[2], dd[3]);
+          *reinterpret_cast<float4 *>(r32o + o) = make_float4(rn[0], rn[1], rn[2], rn[3]);
+          *reinterpret_cast<float4 *>(p32o + o) = make_float4(pn[0], pn[1], pn[2], pn[3]);
+          uint2 ev;
+          ev.x = (uint32_t)(uint16_t)(short)max(-32000, min(en[0], 32000)) |
+                 ((uint32_t)(uint16_t)(short)max(-32000, min(en[1], 32000)) << 16);
+          ev.y = (uint32_t)(uint16_t)(short)max(-32000, min(en[2], 32000)) |
+                 ((uint32_t)(uint16_t)(short)max(-32000, min(en[3], 32000)) << 16);
+          *reinterpret_cast<uint2 *>(e16o + o) = ev;
+        }
+      }
+      A = C;
+      C = B;
+    }
+  }
+  const Acc64 tot = block_acc(to64(acc), shm, shs);
+  float bm = 0.f;
+  if (PASS2) bm = block_maxf(rmax, shf);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = tot.m;
+    part[nblk_part + blockIdx.x] = (double)tot.s;
+    if (PASS2) part[2 * nblk_part + blockIdx.x] = (double)bm;
+  }
+  if (!last_block(&st->counter[PASS2 ? 2 : 1], &flag)) return;
+  const Acc64 sum = sum_acc_partials(part, part + nblk_part, gridDim.x, shm, shs);
+  if (!PASS2) {
+    if (threadIdx.x == 0) {
+      const Acc64 rho{st->rho_m, st->rho_s};
+      if (sum.m > 0.0 && isfinite(sum.m)) {
+        st->alpha = acc_ratio(rho, sum);
+      } else if (rho.m == 0.0) {
+        st->alpha = 0.0;
+        st->done = 1;
+        st->status = EIK_OK;
+      } else {
+        st->alpha = 0.0;
+        st->done = 1;
+        st->status = EIK_ERR_BREAKDOWN;
+      }
+      st->counter[1] = 0u;
+    }
+  } else {
+    const double rm = max_partials(part + 2 * nblk_part, gridDim.x, shm);
+    if (threadIdx.x == 0) {
+      const Acc64 rho{st->rho_m, st->rho_s};
+      st->beta = acc_ratio(sum, rho);
+      st->rho_m = sum.m;
+      st->rho_s = sum.s;
+      st->iter += 1;
+      st->total_iter += 1;
+      if (!isfinite(sum.m) || !isfinite(st->beta)) {
+        st->done = 1;
+        st->status = EIK_ERR_BREAKDOWN;
+      } else if ((st->mode == 0 ? rm <= (double)st->thresh : rm == 0.0) || sum.m == 0.0) {
+        st->done = 1;
+        st->status = EIK_OK;
+      } else if (st->iter >= st->max_iter) {
+        st->done = 1;
+        st->status = EIK_ERR_NOT_CONVERGED;
+      }
+      st->counter[2] = 0u;
+    }
   }
 }
 
@@ -679,6 +960,18 @@ __global__ void k_mixed_epilogue(Grid g, CellGrid cg, const int *__restrict__ kx
   }
 }
 
+// Hat-space FP64 solution xh = xbar 2^-kx (sources: sqrt(c) phi_k), for the
+// FP64 adjoint after a mixed forward solve.
+__global__ void k_mixed_export(Grid g, CellGrid cg, const int *__restrict__ kx,
+                               const double *__restrict__ x64, double *__restrict__ xh) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % g.nx), y = (int)((i / g.nx) % g.ny);
+    const int z = (int)(i / ((int64_t)g.nx * g.ny));
+    xh[i] = x64[i] * pow2d(-kx[cell_of(cg, x, y, z)]);
+  }
+}
+
 }  // namespace
 
 // ====================================================================== host
@@ -687,7 +980,9 @@ struct MixedState {
   TileCount tc;
   CellGrid cg;
   int nblk_stencil = 0, nblk_part = 0, cap = 0;
-  float *s32 = nullptr, *fb = nullptr, *St = nullptr, *d32 = nullptr;
+  bool rows2d = false;           // warp-marched 2D kernels (nx % 4 == 0)
+  int tiles_x = 0, ntiles2d = 0, nblk2d = 0;
+  float *s32 = nullptr, *fb = nullptr, *St = nullptr, *d32 = nullptr, *xref = nullptr;
   float *r32[2] = {nullptr, nullptr}, *p32[2] = {nullptr, nullptr};
   short *e16[2] = {nullptr, nullptr};
   int *kx = nullptr;
@@ -695,6 +990,11 @@ struct MixedState {
   MixState *st = nullptr, *h_st = nullptr;
   cudaGraphExec_t graph = nullptr;
   int64_t launches[8] = {0};
+  // per-launch CUDA-event timing of the inner passes when profiling
+  bool profile = false;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  int64_t timed[8] = {0};
+  double ms[8] = {0};
 };
 
 static const char *kMixedNames[] = {"mixed_setup", "coarse_exponents", "mixed_residual64",
@@ -711,8 +1011,21 @@ int64_t mixed_kernel_launches(const MixedState *m, int k) {
 }
 
 void mixed_reset_launches(MixedState *m) {
-  if (m)
-    for (auto &v : m->launches) v = 0;
+  if (!m) return;
+  for (int k = 0; k < 8; ++k) {
+    m->launches[k] = 0;
+    m->timed[k] = 0;
+    m->ms[k] = 0.0;
+  }
+}
+
+void mixed_set_profiling(MixedState *m, bool on) {
+  if (m) m->profile = on;
+}
+
+void mixed_kernel_time(const MixedState *m, int k, int64_t *timed, double *ms) {
+  *timed = (m && k >= 0 && k < 8) ? m->timed[k] : 0;
+  *ms = (m && k >= 0 && k < 8) ? m->ms[k] : 0.0;
 }
 
 const char *mixed_last_error() { return g_msg.c_str(); }
@@ -760,9 +1073,18 @@ eik_status mixed_create(MixedState **out, const Grid &g, const TileCount &tc, in
   if (per_sm < 1) per_sm = 1;
   m->nblk_stencil = (int)std::min<int64_t>(tc.total, (int64_t)per_sm * num_sms);
   m->cap = num_sms * 8;
-  m->nblk_part = std::max(m->nblk_stencil, m->cap);
+  if (g.ndim == 2 && g.nx % 4 == 0) {
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mixed2d<true>, kWarpsPerBlock * 32, 0);
+    if (per < 1) per = 1;
+    m->rows2d = true;
+    m->tiles_x = (g.nx + 127) / 128;
+    m->ntiles2d = m->tiles_x * ((g.ny + kRowTile - 1) / kRowTile);
+    m->nblk2d = std::min(m->ntiles2d, per * num_sms);
+  }
+  m->nblk_part = std::max(std::max(m->nblk_stencil, m->cap), m->nblk2d);
   const int64_t n = g.n;
-  bool ok = mal(&m->s32, n) && mal(&m->d32, n) && mal(&m->r32[0], n) && mal(&m->r32[1], n) &&
+  bool ok = mal(&m->s32, n) && mal(&m->d32, n) && mal(&m->xref, n) && mal(&m->r32[0], n) && mal(&m->r32[1], n) &&
             mal(&m->p32[0], n) && mal(&m->p32[1], n) && mal(&m->e16[0], n) &&
             mal(&m->e16[1], n) && mal(&m->x64, n) && mal(&m->fb, m->cg.ncell) &&
             mal(&m->St, m->cg.ncell) && mal(&m->kx, m->cg.ncell) &&
@@ -790,7 +1112,9 @@ eik_status mixed_create(MixedState **out, const Grid &g, const TileCount &tc, in
 void mixed_destroy(MixedState *m) {
   if (!m) return;
   if (m->graph) cudaGraphExecDestroy(m->graph);
-  void *ptrs[] = {m->s32, m->fb, m->St, m->d32, m->r32[0], m->r32[1], m->p32[0],
+  for (auto &e : m->ev)
+    if (e) cudaEventDestroy(e);
+  void *ptrs[] = {m->s32, m->xref, m->fb, m->St, m->d32, m->r32[0], m->r32[1], m->p32[0],
                   m->p32[1], m->e16[0], m->e16[1], m->kx, m->x64, m->part, m->st};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -802,33 +1126,50 @@ static void launch_residual(MixedState *m, const MixedArgs &a) {
   if (m->g.ndim == 2)
     k_mixed_residual<2><<<m->nblk_stencil, kThreads, 0, a.stream>>>(
         m->g, m->tc, m->cg, m->kx, a.sig, m->x64, m->r32[0], m->p32[0], m->e16[0], m->d32,
-        m->st, m->part, m->nblk_part);
+        m->xref, m->st, m->part, m->nblk_part);
   else
     k_mixed_residual<3><<<m->nblk_stencil, kThreads, 0, a.stream>>>(
         m->g, m->tc, m->cg, m->kx, a.sig, m->x64, m->r32[0], m->p32[0], m->e16[0], m->d32,
-        m->st, m->part, m->nblk_part);
+        m->xref, m->st, m->part, m->nblk_part);
   m->launches[2]++;
 }
 
-static void launch_iteration(MixedState *m, int set, cudaStream_t s) {
+static void launch_iteration(MixedState *m, int set, cudaStream_t s, bool timed = false) {
   const int a = set, b = 1 - set;
   double *p1 = m->part;
   double *p2 = m->part + 3 * (size_t)m->nblk_part;
-  if (m->g.ndim == 2) {
+  if (m->rows2d) {
+    if (timed) cudaEventRecord(m->ev[0], s);
+    k_mixed2d<false><<<m->nblk2d, kWarpsPerBlock * 32, 0, s>>>(
+        m->g, m->cg, m->tiles_x, m->ntiles2d, m->kx, m->r32[a], m->p32[a], m->e16[a], m->s32,
+        nullptr, nullptr, nullptr, m->d32, m->xref, m->st, p1, m->nblk_part);
+    if (timed) cudaEventRecord(m->ev[1], s);
+    k_mixed2d<true><<<m->nblk2d, kWarpsPerBlock * 32, 0, s>>>(
+        m->g, m->cg, m->tiles_x, m->ntiles2d, m->kx, m->r32[a], m->p32[a], m->e16[a], m->s32,
+        m->r32[b], m->p32[b], m->e16[b], m->d32, m->xref, m->st, p2, m->nblk_part);
+    if (timed) cudaEventRecord(m->ev[2], s);
+    return;
+  }
+  if (timed) cudaEventRecord(m->ev[0], s);
+  if (m->g.ndim == 2)
     k_mixed_pass1<2><<<m->nblk_stencil, kThreads, 0, s>>>(m->g, m->tc, m->r32[a], m->p32[a],
                                                          m->e16[a], m->s32, m->st, p1,
                                                          m->nblk_part);
-    k_mixed_pass2<2><<<m->nblk_stencil, kThreads, 0, s>>>(
-        m->g, m->tc, m->cg, m->kx, m->r32[a], m->p32[a], m->e16[a], m->s32, m->r32[b],
-        m->p32[b], m->e16[b], m->d32, m->st, p2, m->nblk_part);
-  } else {
+  else
     k_mixed_pass1<3><<<m->nblk_stencil, kThreads, 0, s>>>(m->g, m->tc, m->r32[a], m->p32[a],
                                                          m->e16[a], m->s32, m->st, p1,
                                                          m->nblk_part);
+  if (timed) cudaEventRecord(m->ev[1], s);
+  if (m->g.ndim == 2) {
+    k_mixed_pass2<2><<<m->nblk_stencil, kThreads, 0, s>>>(
+        m->g, m->tc, m->cg, m->kx, m->r32[a], m->p32[a], m->e16[a], m->s32, m->r32[b],
+        m->p32[b], m->e16[b], m->d32, m->xref, m->st, p2, m->nblk_part);
+  } else {
     k_mixed_pass2<3><<<m->nblk_stencil, kThreads, 0, s>>>(
         m->g, m->tc, m->cg, m->kx, m->r32[a], m->p32[a], m->e16[a], m->s32, m->r32[b],
-        m->p32[b], m->e16[b], m->d32, m->st, p2, m->nblk_part);
+        m->p32[b], m->e16[b], m->d32, m->xref, m->st, p2, m->nblk_part);
   }
+  if (timed) cudaEventRecord(m->ev[2], s);
 }
 
 static eik_status build_graph(MixedState *m, cudaStream_t s) {
@@ -844,6 +1185,7 @@ static eik_status build_graph(MixedState *m, cudaStream_t s) {
 
 eik_status mixed_solve(MixedState *m, const MixedArgs &a, int *inner_iters, int *outer_iters,
                        double *res_cw, double *res_nw) {
+  static const bool trace = getenv("EIK_TRACE_MIXED") != nullptr;
   const Grid &g = m->g;
   cudaStream_t s = a.stream;
   const int cap = m->cap;
@@ -883,34 +1225,61 @@ eik_status mixed_solve(MixedState *m, const MixedArgs &a, int *inner_iters, int 
     const double cw = m->h_st->cw;
     *res_cw = cw;
     *res_nw = 0.0;
+    if (trace)
+      fprintf(stderr, "[mixed] outer %d total %d cw %.3e r_inf %.3e x_inf %.3e\n", outer, total,
+              cw, m->h_st->r_inf, m->h_st->x_inf);
     if (cw <= tol || m->h_st->rho_m == 0.0) {
       result = EIK_OK;
       break;
     }
     if (outer >= max_outer || total >= a.opt.max_iter) break;
-    if (cw < best_cw * 0.5) {
-      best_cw = cw;
+    // (cw is infinite while some node of the iterate is not positive yet;
+    // progress is then judged only once it is finite)
+    if (!std::isfinite(cw) || cw < 0.5 * best_cw) {
+      if (std::isfinite(cw)) best_cw = cw;
       stall = 0;
-    } else if (outer > 1 && ++stall >= 3) {
+    } else if (++stall >= 2) {
       g_msg = "mixed refinement stopped making progress";
       break;
     }
-    // inner solve on the correction
+    // inner solve on the correction.  First step (no iterate yet): reduce the
+    // residual, in kx units, by `red`.  Later steps: componentwise test
+    // |rhat_i| <= theta |x_i + d_i| with theta = max(tol/2, cw/1000).
     MixState st = *m->h_st;
     st.iter = 0;
     st.done = 0;
     st.status = 0;
     st.beta = 0.0;
     st.max_iter = a.opt.max_iter - total;
-    st.thresh = (float)std::max(red * st.r_inf, 0.3 * tol * st.x_inf);
+    st.mode = (outer == 0 || !std::isfinite(cw)) ? 0 : 1;
+    st.thresh = (float)(red * st.r_inf);
+    st.theta = (float)std::max(0.5 * tol, 1e-3 * cw);
     *m->h_st = st;
     MCK(cudaMemcpyAsync(m->st, m->h_st, sizeof(MixState), cudaMemcpyHostToDevice, s));
-    for (;;) {
-      MCK(cudaGraphLaunch(m->graph, s));
-      m->launches[3] += kInnerGraphIters;
-      m->launches[4] += kInnerGraphIters;
+    if (m->profile && !m->ev[0])
+      for (auto &e : m->ev) MCK(cudaEventCreate(&e));
+    for (int it = 0;; ++it) {
+      if (m->profile) {
+        // one timed iteration per host check: no launch runs past convergence
+        launch_iteration(m, it & 1, s, true);
+        m->launches[3] += 1;
+        m->launches[4] += 1;
+      } else {
+        MCK(cudaGraphLaunch(m->graph, s));
+        m->launches[3] += kInnerGraphIters;
+        m->launches[4] += kInnerGraphIters;
+      }
       MCK(cudaMemcpyAsync(m->h_st, m->st, sizeof(MixState), cudaMemcpyDeviceToHost, s));
       MCK(cudaStreamSynchronize(s));
+      if (m->profile) {
+        float t1 = 0.f, t2 = 0.f;
+        MCK(cudaEventElapsedTime(&t1, m->ev[0], m->ev[1]));
+        MCK(cudaEventElapsedTime(&t2, m->ev[1], m->ev[2]));
+        m->ms[3] += t1;
+        m->ms[4] += t2;
+        m->timed[3] += 1;
+        m->timed[4] += 1;
+      }
       if (m->h_st->done) break;
     }
     total += m->h_st->iter;
@@ -927,6 +1296,14 @@ eik_status mixed_solve(MixedState *m, const MixedArgs &a, int *inner_iters, int 
   *inner_iters = total;
   *outer_iters = outer;
   return result;
+}
+
+eik_status mixed_export_hat(MixedState *m, const MixedArgs &a, double *xh) {
+  const Grid &g = m->g;
+  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((g.n + kThreads - 1) / kThreads, m->cap));
+  k_mixed_export<<<nb, kThreads, 0, a.stream>>>(g, m->cg, m->kx, m->x64, xh);
+  MCK(cudaGetLastError());
+  return EIK_OK;
 }
 
 eik_status mixed_write_outputs(MixedState *m, const MixedArgs &a, double *S, double *phi) {

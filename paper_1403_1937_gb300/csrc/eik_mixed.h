@@ -34,9 +34,13 @@ eik_status mixed_solve(MixedState *m, const MixedArgs &a, int *inner_iters, int 
                        double *res_cw, double *res_nw);
 // Writes S (and phi if non-null) from the refined iterate; device pointers.
 eik_status mixed_write_outputs(MixedState *m, const MixedArgs &a, double *S, double *phi);
+// Writes the refined solution in hat-space FP64 (phi = s * xh) to xh.
+eik_status mixed_export_hat(MixedState *m, const MixedArgs &a, double *xh);
 void mixed_destroy(MixedState *m);
 int64_t mixed_kernel_launches(const MixedState *m, int k);
 void mixed_reset_launches(MixedState *m);
+void mixed_set_profiling(MixedState *m, bool on);
+void mixed_kernel_time(const MixedState *m, int k, int64_t *timed, double *ms);
 const char *mixed_last_error();
 // Name of mixed-mode kernel k (0-based), or NULL past the last one.
 const char *mixed_kernel_name(int k);

@@ -206,6 +206,110 @@ def eik_destroy(handle: Handle) -> None:
         handle._ptr = None
 
 
+class Batch:
+    """Owns one ``eik_batch`` (see ``eik_create_batch``)."""
+
+    def __init__(self, ptr, dims_list, device: bool):
+        self._ptr = ptr
+        self.dims = [tuple(d) for d in dims_list]
+        self.sizes = [int(np.prod(d)) for d in self.dims]
+        self.offsets = np.concatenate([[0], np.cumsum(self.sizes)]).astype(np.int64)
+        self.n = int(self.offsets[-1])
+        self.device = device
+
+    @property
+    def ptr(self):
+        if not self._ptr:
+            raise RuntimeError("batch already destroyed")
+        return self._ptr
+
+    def split(self, flat):
+        return [flat[self.offsets[i]:self.offsets[i + 1]].reshape(self.dims[i][::-1])
+                for i in range(len(self.dims))]
+
+    def __del__(self):
+        try:
+            eik_destroy_batch(self)
+        except Exception:
+            pass
+
+
+def eik_create_batch(instances, options: Optional[_lib.Options] = None, stream=None,
+                     device: bool = True, workers: int = 0) -> Batch:
+    """Creates a batch of independent solves (C: ``eik_create_batch``).
+    ``instances`` are objects with dims, h, hbar, f, src_idx, src_U (e.g.
+    ``workloads.Instance``).  With ``device`` the concatenated inputs are
+    staged in device memory first."""
+    lib = _lib.load()
+    ndim = len(instances[0].dims)
+    if any(len(i.dims) != ndim for i in instances):
+        raise ValueError("all instances need the same ndim")
+    dims = np.array([list(i.dims) for i in instances], dtype=np.int64).ravel()
+    hs = np.array([i.h for i in instances], dtype=np.float64)
+    hbars = np.array([i.hbar for i in instances], dtype=np.float64)
+    f = np.concatenate([np.ascontiguousarray(i.f, dtype=np.float64).ravel() for i in instances])
+    src = np.concatenate([np.asarray(i.src_idx, dtype=np.int64).ravel() for i in instances])
+    U = np.concatenate([np.asarray(i.src_U, dtype=np.float64).ravel() for i in instances])
+    so = np.concatenate([[0], np.cumsum([len(np.asarray(i.src_idx).ravel())
+                                         for i in instances])]).astype(np.int64)
+    if device and torch is not None and torch.cuda.is_available():
+        f_arg = torch.from_numpy(f).cuda()
+    else:
+        f_arg = f
+    fp, fk = _ptr(f_arg, np.float64, "f")
+    out = ctypes.c_void_p()
+    opt = options if options is not None else _lib.default_options()
+    st = lib.eik_create_batch(
+        ctypes.byref(out), len(instances), ndim,
+        dims.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+        hs.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+        hbars.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), fp,
+        ctypes.c_void_p(so.ctypes.data), ctypes.c_void_p(src.ctypes.data),
+        ctypes.c_void_p(U.ctypes.data), ctypes.byref(opt), _stream_ptr(stream))
+    _lib.check(st)
+    b = Batch(out, [i.dims for i in instances], device)
+    if workers:
+        _lib.check(lib.eik_batch_set_concurrency(b.ptr, int(workers)))
+    return b
+
+
+def eik_set_f_batch(batch: Batch, f) -> None:
+    fp, fk = _ptr(f, np.float64, "f")
+    _lib.check(_lib.load().eik_set_f_batch(batch.ptr, fp))
+
+
+def eik_solve_batch(batch: Batch, S_out=None, allow_not_converged: bool = False):
+    """Solves every instance; returns (S concatenated, list of stats dicts)."""
+    if S_out is None:
+        if batch.device and torch is not None:
+            S_out = torch.empty(batch.n, dtype=torch.float64, device="cuda")
+        else:
+            S_out = np.empty(batch.n, dtype=np.float64)
+    sp, sk = _ptr(S_out, np.float64, "S_out")
+    stats = (_lib.Stats * len(batch.dims))()
+    st = _lib.load().eik_solve_batch(batch.ptr, sp, ctypes.cast(stats, ctypes.c_void_p))
+    allow = (_lib.EIK_OK, _lib.EIK_ERR_NOT_CONVERGED) if allow_not_converged else (_lib.EIK_OK,)
+    _lib.check(st, allow)
+    return S_out, [s.as_dict() for s in stats]
+
+
+def eik_grad_batch(batch: Batch, dLdS, dLdf_out=None):
+    if dLdf_out is None:
+        dLdf_out = (torch.empty_like(dLdS) if _is_torch(dLdS)
+                    else np.empty(batch.n, dtype=np.float64))
+    ip, ik = _ptr(dLdS, np.float64, "dLdS")
+    op, ok = _ptr(dLdf_out, np.float64, "dLdf")
+    stats = (_lib.Stats * len(batch.dims))()
+    _lib.check(_lib.load().eik_grad_batch(batch.ptr, ip, op, ctypes.cast(stats, ctypes.c_void_p)))
+    return dLdf_out, [s.as_dict() for s in stats]
+
+
+def eik_destroy_batch(batch: Batch) -> None:
+    if batch is not None and batch._ptr:
+        _lib.load().eik_destroy_batch(batch._ptr)
+        batch._ptr = None
+
+
 def solve(f, h: float, hbar: float, src_idx, src_U=None, precision: str = "fp64",
           tol: Optional[float] = None, want_phi: bool = False, **kw):
     """One-shot convenience: dims are taken from the array shape (numpy order

@@ -78,9 +78,9 @@ def test_c3_reduced_mixed(eik):
 
 @pytest.mark.parametrize("n,mult,corner", [(400, 2, True), (300, 2, False)])
 def test_underflowing_phi(eik, n, mult, corner):
-    """hbar = 2h with f up to 1.5: S/hbar reaches several hundred, phi
-    underflows FP32 everywhere and FP64 in the far corner; the oracle solves
-    the diagonally similar relative form."""
+    """hbar = 2h with f up to 1.5: S/hbar reaches a few hundred, so phi
+    underflows FP32 far below its range; the oracle solves the diagonally
+    similar relative form."""
     rng = np.random.default_rng(n + mult)
     dims = (n, n)
     h = 1.0 / (n - 1)
@@ -90,27 +90,28 @@ def test_underflowing_phi(eik, n, mult, corner):
     S, _, stats, _ = mixed_solve(eik, inst)
     sys = fd.assemble(inst.f, inst.dims, inst.h, inst.hbar, inst.src_idx)
     S_ref = fd.solve_relative(sys)
-    assert np.max(S_ref) / inst.hbar > 300
+    assert np.max(S_ref) / inst.hbar > 100
     assert np.max(np.abs(S - S_ref)) <= S_ABS
 
 
 @pytest.mark.slow
 def test_c2_full_size_mixed(eik):
-    """Config 2 at 2048^2 in the bench's configuration (tol 1e-8)."""
+    """Config 2 at 2048^2 in the bench's configuration (tol 1e-6)."""
     inst = wl.config2()
-    S, _, stats, _ = mixed_solve(eik, inst, tol=1e-8)
+    S, _, stats, _ = mixed_solve(eik, inst, tol=1e-6)
     S_ref, _, _, info = cg.solve(inst.f, inst.dims, inst.h, inst.hbar, inst.src_idx,
                                  tol=1e-13)
     assert info["status"] == 0
     assert np.max(np.abs(S - S_ref)) <= S_ABS
 
 
-def test_fp64_at_bench_tolerance(eik):
-    """The plain FP64 path at the bench tolerance (1e-8) also meets S <= 1e-6
-    (reduced size, direct oracle)."""
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_bench_tolerance_meets_S_bound(eik, precision):
+    """Both precision modes at the bench tolerance (componentwise 1e-6) meet
+    S <= 1e-6 against the direct oracle (config 2 structure at 768^2)."""
     import torch
     inst = wl.config2(n=768)
-    opt = eik.make_options(precision="fp64", tol=1e-8)
+    opt = eik.make_options(precision=precision, tol=1e-6)
     f = torch.from_numpy(inst.f).cuda()
     h = eik.eik_create(inst.dims, inst.h, inst.hbar, f, inst.src_idx, None, opt)
     S, _, _ = eik.eik_solve(h)
