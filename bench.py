@@ -51,7 +51,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4"])
+    ap.add_argument("--c4-count", type=int, default=256,
+                    help="instances in the batched workload (c4)")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -269,6 +271,57 @@ def run_ours(args):
     return inst, desc, n_unk, results, ws, rank
 
 
+def run_batch(args):
+    """Batched workload: independent 2D instances of uneven size, f, sources
+    and hbar (config 4), solved together through eik_solve_batch."""
+    import torch
+    from paper_1403_1937_gb300 import build as _build
+    if not _build.up_to_date():
+        _build.build()
+    from paper_1403_1937_gb300 import eik
+    from paper_1403_1937_gb300 import workloads as wl
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    insts = wl.config4(count=args.c4_count)
+    n_unk = [i.n - len(np.unique(i.src_idx)) for i in insts]
+    opt = eik.make_options(precision=args.precision, tol=args.tol)
+    b = eik.eik_create_batch(insts, opt)
+    S = torch.empty(b.n, dtype=torch.float64, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        eik.eik_solve_batch(b, S_out=S)
+    times, units = [], 0
+    with Clocks(local) as clk:
+        for _ in range(args.steps):
+            flush_l2(flush)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, stats = eik.eik_solve_batch(b, S_out=S)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+            units += sum(u * st["inner_iters"] for u, st in zip(n_unk, stats))
+    total = sum(times)
+    line = {"metric": METRIC, "value": round(units / total / 1e9, 4), "unit": UNIT,
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * total / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+            "config": {"workload": f"batched 2D: {len(insts)} instances, sides 64..1024, "
+                                   "Fourier f in [0.5,1.5], 1-8 sources, hbar in {2h,4h,8h}",
+                       "instances": len(insts), "nodes": int(b.n), "precision": args.precision,
+                       "tol_componentwise": args.tol,
+                       "l2": "flushed between steps (256 MiB write)"},
+            "clocks": clk.summary(),
+            "iterations": {"min": min(s_["inner_iters"] for s_ in stats),
+                           "max": max(s_["inner_iters"] for s_ in stats)}}
+    eik.eik_destroy_batch(b)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def roofline(res, inst, wname):
     peak, peak_src = measured_peaks()
     km = {k: v for k, v in res["kernel_ms"].items() if v[0] is not None}
@@ -337,6 +390,9 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "c4":
+        run_batch(args)
         return
     inst, desc, n_unk, results, ws, rank = run_ours(args)
     if rank != 0:

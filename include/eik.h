@@ -88,7 +88,8 @@ typedef struct {
   int max_iter;       /* CG iterations (total over refinement steps); default
                          200000 */
   int boundary;       /* EIK_BOUNDARY_*; default half cell */
-  int tile_override;  /* 0 = library choice; reserved for tile selection */
+  int tile_override;  /* kernel variant: 0 = library choice; 1 = generic
+                         halo-tile kernels everywhere (mixed mode) */
   double inner_tol;   /* mixed mode: componentwise tolerance of each FP32
                          inner solve; 0 = library choice */
   int max_outer;      /* mixed mode: refinement steps; 0 = library choice */

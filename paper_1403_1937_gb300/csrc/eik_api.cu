@@ -525,7 +525,7 @@ eik_status eik_create(eik_handle **out, int ndim, const int64_t *dims, double hs
                        h->stream));
     CK(cudaStreamSynchronize(h->stream));
     if (o.precision == EIK_PREC_MIXED) {
-      eik_status ms = mixed_create(&h->mixed, g, h->tc, h->num_sms, h->stream);
+      eik_status ms = mixed_create(&h->mixed, g, h->tc, h->num_sms, o.tile_override, h->stream);
       if (ms != EIK_OK) {
         free_handle(h);
         return fail(ms, "mixed-precision workspace allocation failed");

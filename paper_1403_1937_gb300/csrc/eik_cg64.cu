@@ -306,7 +306,10 @@ k_pass2_64(int64_t n, double *__restrict__ x, double *__restrict__ r,
       if (cw_weight) {
         // weighted absolute test |w_i r_i| <= tol (adjoint solve)
         if (!(fabs(cw_weight[i] * rn) <= tol)) bad = 1.0;
-      } else if (!(fabs(rn) <= tol * xn && xn > 0.0)) {
+      } else if (!(fabs(rn) <= tol * fabs(xn))) {
+        // |x| rather than x > 0: where rounding in the iterate left x <= 0
+        // while the recurrence residual is already tiny, the loop ends and
+        // the true residual (which counts x <= 0 as unconverged) restarts it
         bad = 1.0;
       }
     }

@@ -30,6 +30,7 @@
 
 #include <cmath>
 #include <string>
+#include <vector>
 
 #include "eik_launch.h"
 #include "eik_mixed.h"
@@ -42,7 +43,7 @@ constexpr int kInnerGraphIters = 32;   // even: the buffer sets alternate
 constexpr int kNoExp = 30000;          // exponent of an all-zero node
 constexpr int kMaxCells = 16384;
 
-std::string g_msg = "no error";
+thread_local std::string g_msg = "no error";   // per host thread (batches)
 
 // ------------------------------------------------------------ exponents
 // 2^n as a float; 0 below the normal range, 2^127 above it.
@@ -688,7 +689,8 @@ k_mixed_pass2(Grid g, TileCount tc, CellGrid cg, const int *__restrict__ kx,
 // by warp shuffle (lanes 0 and 31 load the column beyond the warp).  No shared
 // memory and no block barrier on the data path; the next row's loads are
 // issued before the current row is computed.  Arithmetic is that of
-// stencil_q / k_mixed_pass1 / k_mixed_pass2 above.
+// stencil_q / k_mixed_pass1 / k_mixed_pass2 above; inner-product terms are
+// accumulated node by node, as there.
 constexpr int kRowsPerWarp = 4;
 constexpr int kWarpsPerBlock = 8;
 constexpr int kRowTile = kRowsPerWarp * kWarpsPerBlock;   // rows per block tile
@@ -810,11 +812,10 @@ k_mixed2d(Grid g, CellGrid cg, int tiles_x, int ntiles, const int *__restrict__ 
                                 B.e3, hx3, hy, E3);
         if (!PASS2) {
           // <phat, qhat>: terms pt*q 2^-(e+E); align to the largest scale
-          const int t0 = -(C.e0 + E0), t1 = -(C.e1 + E1), t2 = -(C.e2 + E2), t3 = -(C.e3 + E3);
-          const int tm = max(max(t0, t1), max(t2, t3));
-          const float sum = C.pt.x * q0 * pow2f(t0 - tm) + C.pt.y * q1 * pow2f(t1 - tm) +
-                            C.pt.z * q2 * pow2f(t2 - tm) + C.pt.w * q3 * pow2f(t3 - tm);
-          acc_add(acc, sum, tm);
+          acc_add(acc, C.pt.x * q0, -(C.e0 + E0));
+          acc_add(acc, C.pt.y * q1, -(C.e1 + E1));
+          acc_add(acc, C.pt.z * q2, -(C.e2 + E2));
+          acc_add(acc, C.pt.w * q3, -(C.e3 + E3));
         } else {
           const int64_t o = (int64_t)y * g.nx + x;
           const int ki = kx[(x >> cg.lgB) + cg.cx * (y >> cg.lgB)];
@@ -848,11 +849,8 @@ k_mixed2d(Grid g, CellGrid cg, int tiles_x, int ntiles, const int *__restrict__ 
             }
           }
           // <rhat, rhat> terms rn^2 2^-2en
-          const int t0 = -2 * en[0], t1 = -2 * en[1], t2 = -2 * en[2], t3 = -2 * en[3];
-          const int tm = max(max(t0, t1), max(t2, t3));
-          const float sum = rn[0] * rn[0] * pow2f(t0 - tm) + rn[1] * rn[1] * pow2f(t1 - tm) +
-                            rn[2] * rn[2] * pow2f(t2 - tm) + rn[3] * rn[3] * pow2f(t3 - tm);
-          acc_add(acc, sum, tm);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc_add(acc, rn[j] * rn[j], -2 * en[j]);
           float4 xr = make_float4(0.f, 0.f, 0.f, 0.f);
           if (mode != 0) xr = ld4(xref + o);
           const float xrs[4] = {xr.x, xr.y, xr.z, xr.w};
@@ -1045,7 +1043,7 @@ static bool mal(T **p, size_t n) {
 }
 
 eik_status mixed_create(MixedState **out, const Grid &g, const TileCount &tc, int num_sms,
-                        cudaStream_t s) {
+                        int tile_override, cudaStream_t s) {
   MixedState *m = new MixedState();
   m->g = g;
   m->tc = tc;
@@ -1073,7 +1071,8 @@ eik_status mixed_create(MixedState **out, const Grid &g, const TileCount &tc, in
   if (per_sm < 1) per_sm = 1;
   m->nblk_stencil = (int)std::min<int64_t>(tc.total, (int64_t)per_sm * num_sms);
   m->cap = num_sms * 8;
-  if (g.ndim == 2 && g.nx % 4 == 0) {
+  // tile_override == 1 selects the generic halo-tile kernels everywhere
+  if (g.ndim == 2 && g.nx % 4 == 0 && tile_override != 1) {
     int per = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mixed2d<true>, kWarpsPerBlock * 32, 0);
     if (per < 1) per = 1;
@@ -1259,6 +1258,15 @@ eik_status mixed_solve(MixedState *m, const MixedArgs &a, int *inner_iters, int 
     if (m->profile && !m->ev[0])
       for (auto &e : m->ev) MCK(cudaEventCreate(&e));
     for (int it = 0;; ++it) {
+      if (trace && it < 6) {
+        launch_iteration(m, it & 1, s);
+        MCK(cudaMemcpyAsync(m->h_st, m->st, sizeof(MixState), cudaMemcpyDeviceToHost, s));
+        MCK(cudaStreamSynchronize(s));
+        fprintf(stderr, "[mixed]   it %d alpha %.9e beta %.9e rho %.9e*2^%d\n", m->h_st->iter,
+                m->h_st->alpha, m->h_st->beta, m->h_st->rho_m, m->h_st->rho_s);
+        if (m->h_st->done) break;
+        continue;   // six traced iterations: the graph resumes on buffer set 0
+      }
       if (m->profile) {
         // one timed iteration per host check: no launch runs past convergence
         launch_iteration(m, it & 1, s, true);

@@ -29,7 +29,7 @@ struct MixedArgs {
 };
 
 eik_status mixed_create(MixedState **out, const Grid &g, const TileCount &tc, int num_sms,
-                        cudaStream_t s);
+                        int tile_override, cudaStream_t s);
 eik_status mixed_solve(MixedState *m, const MixedArgs &a, int *inner_iters, int *outer_iters,
                        double *res_cw, double *res_nw);
 // Writes S (and phi if non-null) from the refined iterate; device pointers.
