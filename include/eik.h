@@ -185,6 +185,41 @@ eik_status eik_destroy_batch(eik_batch *b);
 /* Instances solved concurrently (host worker threads); 0 = library choice. */
 eik_status eik_batch_set_concurrency(eik_batch *b, int workers);
 
+/*
+ * Componentwise residual of a given S without allocating any device memory
+ * (the paper has no counterpart; this is a service for callers that cannot
+ * allocate).  Code that runs inside a memory pool or arena that must not
+ * grow, allocator hooks or plugins that may not call back into cudaMalloc,
+ * and real-time loops that cannot afford cudaMalloc's implicit device
+ * synchronisation can still check a solution with it.
+ *
+ * Computes max over non-source nodes of
+ *   | (c / a_i) sum_{j~i} omega_ij exp((S_i - S_j)/hbar) - 1 |,  c = hbar^2/h^2,
+ * which is |r_i| / (a_i phi_i) for phi = exp(-S/hbar) -- the quantity
+ * eik_solve reports as eik_stats.res_cw -- and writes it to *res_max.
+ *   ndim, dims, h, hbar, boundary   as for eik_create
+ *   f, S        N = prod(dims) device values (forcing field, solution)
+ *   src_idx     nsrc device indices of the source nodes (skipped); an index
+ *               outside the grid makes the result NaN
+ *   res_max     one device double (written asynchronously)
+ *   stream      stream the work is queued on; the call does not synchronise
+ * All pointers must be device pointers.  Returns EIK_ERR_ARG for invalid
+ * arguments, including grids of more than 1048576 (2^20) nodes, which do not
+ * fit the fixed working memory; EIK_ERR_CUDA on a CUDA error.
+ *
+ * Working memory: one file-scope device array of about 8.4 MB, held by every
+ * GPU that loads the library until the process exits.  Nothing is allocated
+ * or freed.  The first call on each device looks up that array's device
+ * address (once per device, with the device current); make that first call
+ * before any stream capture.  All calls share the array, so calls whose work
+ * overlaps on the GPU (different streams, or host threads without ordering)
+ * race and may return wrong results; order them on one stream.
+ */
+eik_status eik_residual_noalloc(int ndim, const int64_t *dims, double h, double hbar,
+                                const double *f, const double *S, const int64_t *src_idx,
+                                int64_t nsrc, int boundary, double *res_max,
+                                eik_stream_t stream);
+
 /* Per-kernel counters of a handle (diagnostics; the paper has no
  * counterpart).  launches counts every kernel launch the handle issued since
  * creation or the last eik_reset_kernel_stats (kernels inside captured graphs

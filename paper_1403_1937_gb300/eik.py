@@ -311,6 +311,30 @@ def eik_destroy_batch(batch: Batch) -> None:
         batch._ptr = None
 
 
+def eik_residual_noalloc(dims: Sequence[int], h: float, hbar: float, f, S, src_idx,
+                         res_max, boundary: str = "half_cell", stream=None) -> None:
+    """Componentwise residual max of S written to the one-element device
+    tensor ``res_max``, without any device allocation by the library (C:
+    ``eik_residual_noalloc``).  ``f``, ``S``, ``src_idx`` and ``res_max``
+    must be CUDA tensors; grids are limited to 2**20 nodes.  The work is
+    queued on ``stream`` (default: the current torch stream) and not awaited."""
+    dims = tuple(int(d) for d in dims)
+    for name, a in (("f", f), ("S", S), ("src_idx", src_idx), ("res_max", res_max)):
+        if not (_is_torch(a) and a.is_cuda):
+            raise TypeError(f"{name} must be a CUDA tensor")
+    fp, fk = _ptr(f, np.float64, "f")
+    sp, sk = _ptr(S, np.float64, "S")
+    ip, ik = _ptr(src_idx, np.int64, "src_idx")
+    rp, rk = _ptr(res_max, np.float64, "res_max")
+    darr = (ctypes.c_int64 * len(dims))(*dims)
+    b = {"half_cell": _lib.BOUNDARY_HALF_CELL, "drop_edge": _lib.BOUNDARY_DROP_EDGE}[boundary]
+    st = _lib.load().eik_residual_noalloc(len(dims), darr, float(h), float(hbar), fp, sp, ip,
+                                          _numel(src_idx), b, rp, _stream_ptr(stream))
+    if st != _lib.EIK_OK:
+        raise _lib.EikError(st, "eik_residual_noalloc failed (grids are limited to 2**20 "
+                                "nodes; pointers must be device pointers)")
+
+
 def solve(f, h: float, hbar: float, src_idx, src_U=None, precision: str = "fp64",
           tol: Optional[float] = None, want_phi: bool = False, **kw):
     """One-shot convenience: dims are taken from the array shape (numpy order
