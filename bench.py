@@ -50,11 +50,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4"])
     ap.add_argument("--c4-count", type=int, default=256,
                     help="instances in the batched workload (c4)")
     ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--tile-override", type=int, default=0,
+                    help="kernel variant (eik_options.tile_override): 0 library choice, "
+                         "1 generic halo tiles, 2 four columns per lane in 2D")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=0,
@@ -196,7 +199,7 @@ def run_ours(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
 
     def make(prec):
-        opt = eik.make_options(precision=prec, tol=args.tol)
+        opt = eik.make_options(precision=prec, tol=args.tol, tile_override=args.tile_override)
         return eik.eik_create(inst.dims, inst.h, inst.hbar, f_dev, src, None, opt)
 
     modes = [args.precision] + [m for m in ("fp64", "mixed") if m != args.precision]
@@ -284,7 +287,8 @@ def run_batch(args):
     torch.cuda.set_device(local)
     insts = wl.config4(count=args.c4_count)
     n_unk = [i.n - len(np.unique(i.src_idx)) for i in insts]
-    opt = eik.make_options(precision=args.precision, tol=args.tol)
+    opt = eik.make_options(precision=args.precision, tol=args.tol,
+                           tile_override=args.tile_override)
     b = eik.eik_create_batch(insts, opt)
     S = torch.empty(b.n, dtype=torch.float64, device="cuda")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")

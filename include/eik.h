@@ -88,11 +88,23 @@ typedef struct {
   int max_iter;       /* CG iterations (total over refinement steps); default
                          200000 */
   int boundary;       /* EIK_BOUNDARY_*; default half cell */
-  int tile_override;  /* kernel variant: 0 = library choice; 1 = generic
-                         halo-tile kernels everywhere (mixed mode) */
-  double inner_tol;   /* mixed mode: componentwise tolerance of each FP32
-                         inner solve; 0 = library choice */
-  int max_outer;      /* mixed mode: refinement steps; 0 = library choice */
+  int tile_override;  /* mixed-mode inner-CG kernel variant (results agree
+                         to rounding; for tuning and tests):
+                         0 = library choice (2D with nx % 8 == 0: TMA-staged
+                             tiles of 128 x 16 nodes; other even nx:
+                             warp-marched rows; otherwise generic);
+                         1 = generic halo-tile kernels everywhere;
+                         2 / 3 = warp-marched rows, 4 / 2 columns per lane
+                             (2D, nx divisible by that);
+                         4..7 = TMA-staged tiles (2D, nx % 8 == 0) with
+                             (rows per tile, warps per block) = (16, 4),
+                             (32, 8), (16, 8), (32, 4).
+                         A variant whose condition fails falls back to the
+                         generic kernels. */
+  double inner_tol;   /* mixed mode: factor by which the first FP32 inner
+                         solve reduces the residual (scaled max norm);
+                         0 = library choice (1e-3) */
+  int max_outer;      /* mixed mode: refinement steps; 0 = library choice (30) */
   int reserved[7];
 } eik_options;
 

@@ -24,6 +24,7 @@
 // than the final values, whose cancellation FP32 cannot carry.  Refinement
 // repairs this: each outer step forms the true FP64 residual in relative
 // form and solves for a correction with a fresh inner CG.
+#include <cuda.h>
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -168,7 +169,7 @@ struct MixState {
   int done;
   int status;
   int total_iter;
-  int pad;
+  int fault;         // a bounded device-side wait expired (see k_mixed2d_tma)
   unsigned int counter[4];
   // outputs of the relative-form FP64 residual
   double cw;         // max |r|/(a phi) over the unknowns
@@ -683,8 +684,9 @@ k_mixed_pass2(Grid g, TileCount tc, CellGrid cg, const int *__restrict__ kx,
 }
 
 // ------------------------------------------- 2D inner CG, warp-marched rows
-// Specialisation for 2D grids with nx % 4 == 0: a warp owns 128 consecutive
-// columns (4 per lane, float4 loads) and marches down kRowsPerWarp rows,
+// Specialisation for 2D grids with nx % VEC == 0: a warp owns 32*VEC
+// consecutive columns (VEC = 2 or 4 per lane, vector loads) and marches down
+// kRowsPerWarp rows,
 // keeping the rows above and below in registers and taking the x neighbours
 // by warp shuffle (lanes 0 and 31 load the column beyond the warp).  No shared
 // memory and no block barrier on the data path; the next row's loads are
@@ -695,45 +697,89 @@ constexpr int kRowsPerWarp = 4;
 constexpr int kWarpsPerBlock = 8;
 constexpr int kRowTile = kRowsPerWarp * kWarpsPerBlock;   // rows per block tile
 
+// Row of a warp: VEC consecutive columns per lane (VEC = 2 or 4), plus the
+// u/e of the column left of the lane's first and right of its last.
+template <int VEC>
 struct Row {
-  float4 r, pt, s, u;
-  int e0, e1, e2, e3;
+  float r[VEC], pt[VEC], s[VEC], u[VEC];
+  int e[VEC];
   float uL, uR;
   int eL, eR;
 };
 
-__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+template <int VEC>
+__device__ __forceinline__ void ldv(const float *p, float (&v)[VEC]) {
+  if (VEC == 4) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  } else {
+    const float2 t = *reinterpret_cast<const float2 *>(p);
+    v[0] = t.x; v[1] = t.y;
+  }
+}
+template <int VEC>
+__device__ __forceinline__ void stv(float *p, const float (&v)[VEC]) {
+  if (VEC == 4)
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  else
+    *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+}
+template <int VEC>
+__device__ __forceinline__ void lde(const short *p, int (&v)[VEC]) {
+  if (VEC == 4) {
+    const uint2 t = *reinterpret_cast<const uint2 *>(p);
+    v[0] = (short)(t.x & 0xffff); v[1] = (short)(t.x >> 16);
+    v[2] = (short)(t.y & 0xffff); v[3] = (short)(t.y >> 16);
+  } else {
+    const unsigned int t = *reinterpret_cast<const unsigned int *>(p);
+    v[0] = (short)(t & 0xffff); v[1] = (short)(t >> 16);
+  }
+}
+__device__ __forceinline__ uint32_t pack2(int a, int b) {
+  return (uint32_t)(uint16_t)(short)max(-32000, min(a, 32000)) |
+         ((uint32_t)(uint16_t)(short)max(-32000, min(b, 32000)) << 16);
+}
+template <int VEC>
+__device__ __forceinline__ void ste(short *p, const int (&v)[VEC]) {
+  if (VEC == 4)
+    *reinterpret_cast<uint2 *>(p) = make_uint2(pack2(v[0], v[1]), pack2(v[2], v[3]));
+  else
+    *reinterpret_cast<unsigned int *>(p) = pack2(v[0], v[1]);
+}
 
+template <int VEC>
 __device__ __forceinline__ void load_row(const Grid &g, int x, int xw, int y, float beta,
                                          const float *__restrict__ r32,
                                          const float *__restrict__ p32,
                                          const short *__restrict__ e16,
-                                         const float *__restrict__ s32, Row &R) {
+                                         const float *__restrict__ s32, Row<VEC> &R) {
   const int lane = threadIdx.x & 31;
   const bool in = (y >= 0) && (y < g.ny) && (x < g.nx);
   if (in) {
     const int64_t o = (int64_t)y * g.nx + x;
-    R.r = ld4(r32 + o);
-    const float4 p = ld4(p32 + o);
-    R.s = ld4(s32 + o);
-    const uint2 ev = *reinterpret_cast<const uint2 *>(e16 + o);
-    R.e0 = (short)(ev.x & 0xffff);
-    R.e1 = (short)(ev.x >> 16);
-    R.e2 = (short)(ev.y & 0xffff);
-    R.e3 = (short)(ev.y >> 16);
-    R.pt = make_float4(fmaf(beta, p.x, R.r.x), fmaf(beta, p.y, R.r.y), fmaf(beta, p.z, R.r.z),
-                       fmaf(beta, p.w, R.r.w));
-    R.u = make_float4(R.s.x * R.pt.x, R.s.y * R.pt.y, R.s.z * R.pt.z, R.s.w * R.pt.w);
+    float p[VEC];
+    ldv<VEC>(r32 + o, R.r);
+    ldv<VEC>(p32 + o, p);
+    ldv<VEC>(s32 + o, R.s);
+    lde<VEC>(e16 + o, R.e);
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+      R.pt[j] = fmaf(beta, p[j], R.r[j]);
+      R.u[j] = R.s[j] * R.pt[j];
+    }
   } else {
-    R.r = R.pt = R.s = R.u = make_float4(0.f, 0.f, 0.f, 0.f);
-    R.e0 = R.e1 = R.e2 = R.e3 = kNoExp;
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+      R.r[j] = R.pt[j] = R.s[j] = R.u[j] = 0.f;
+      R.e[j] = kNoExp;
+    }
   }
-  R.uL = __shfl_up_sync(0xffffffffu, R.u.w, 1);
-  R.eL = __shfl_up_sync(0xffffffffu, R.e3, 1);
-  R.uR = __shfl_down_sync(0xffffffffu, R.u.x, 1);
-  R.eR = __shfl_down_sync(0xffffffffu, R.e0, 1);
+  R.uL = __shfl_up_sync(0xffffffffu, R.u[VEC - 1], 1);
+  R.eL = __shfl_up_sync(0xffffffffu, R.e[VEC - 1], 1);
+  R.uR = __shfl_down_sync(0xffffffffu, R.u[0], 1);
+  R.eR = __shfl_down_sync(0xffffffffu, R.e[0], 1);
   if (lane == 0 || lane == 31) {
-    const int xn = (lane == 0) ? xw - 1 : xw + 128;
+    const int xn = (lane == 0) ? xw - 1 : xw + 32 * VEC;
     float uu = 0.f;
     int ee = kNoExp;
     if (y >= 0 && y < g.ny && xn >= 0 && xn < g.nx) {
@@ -751,8 +797,7 @@ __device__ __forceinline__ void load_row(const Grid &g, int x, int xw, int y, fl
   }
 }
 
-// q for column j of the current row (E returned); u/e of the x neighbours,
-// the row above (a) and below (b).
+// q for one column: u/e of the x neighbours, the row above (a) and below (b).
 __device__ __forceinline__ float q_node(float pt, float sg, int ei, float uL, int eL, float uR,
                                         int eR, float ua, int ea, float ub, int eb, float hx,
                                         float hy, int &E) {
@@ -763,121 +808,16 @@ __device__ __forceinline__ float q_node(float pt, float sg, int ei, float uL, in
   return fmaf(-sg, fmaf(hy, a1, hx * a2), pt * pow2f(m - ei));
 }
 
+// End of an inner pass: block partials of the inner product (and, in pass
+// 2, of the residual maximum), then the last block forms alpha (pass 1) or
+// beta and the stopping decision (pass 2).
 template <bool PASS2>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
-k_mixed2d(Grid g, CellGrid cg, int tiles_x, int ntiles, const int *__restrict__ kx,
-          const float *__restrict__ r32, const float *__restrict__ p32,
-          const short *__restrict__ e16, const float *__restrict__ s32,
-          float *__restrict__ r32o, float *__restrict__ p32o, short *__restrict__ e16o,
-          float *__restrict__ d32, const float *__restrict__ xref, MixState *st, double *part,
-          int nblk_part) {
+__device__ void inner_pass_tail(const Acc32 &acc, float rmax, MixState *st, double *part,
+                                int nblk_part) {
   __shared__ double shm[32];
   __shared__ int shs[32];
   __shared__ float shf[32];
   __shared__ int flag;
-  if (st->done) return;
-  const float beta = (float)st->beta, alpha = (float)st->alpha;
-  const int mode = st->mode;
-  const float theta = st->theta;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const bool half = g.boundary == EIK_BOUNDARY_HALF_CELL;
-  Acc32 acc{0.f, 0};
-  float rmax = 0.f;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int xw = (t % tiles_x) * 128;
-    const int x = xw + 4 * lane;
-    const int y0 = (t / tiles_x) * kRowTile + warp * kRowsPerWarp;
-    if (y0 >= g.ny) continue;   // whole warp: uniform
-    // face weights of the 4 columns (x edges carry hy, y edges hx)
-    const float hx0 = (half && (x == 0 || x == g.nx - 1)) ? 0.5f : 1.f;
-    const float hx1 = (half && (x + 1 == g.nx - 1)) ? 0.5f : 1.f;
-    const float hx2 = (half && (x + 2 == g.nx - 1)) ? 0.5f : 1.f;
-    const float hx3 = (half && (x + 3 == g.nx - 1)) ? 0.5f : 1.f;
-    Row A, C, B;   // above, current, below
-    load_row(g, x, xw, y0 - 1, beta, r32, p32, e16, s32, A);
-    load_row(g, x, xw, y0, beta, r32, p32, e16, s32, C);
-    for (int k = 0; k < kRowsPerWarp; ++k) {
-      const int y = y0 + k;
-      load_row(g, x, xw, y + 1, beta, r32, p32, e16, s32, B);
-      if (y < g.ny && x < g.nx) {
-        const float hy = (half && (y == 0 || y == g.ny - 1)) ? 0.5f : 1.f;
-        int E0, E1, E2, E3;
-        const float q0 = q_node(C.pt.x, C.s.x, C.e0, C.uL, C.eL, C.u.y, C.e1, A.u.x, A.e0, B.u.x,
-                                B.e0, hx0, hy, E0);
-        const float q1 = q_node(C.pt.y, C.s.y, C.e1, C.u.x, C.e0, C.u.z, C.e2, A.u.y, A.e1, B.u.y,
-                                B.e1, hx1, hy, E1);
-        const float q2 = q_node(C.pt.z, C.s.z, C.e2, C.u.y, C.e1, C.u.w, C.e3, A.u.z, A.e2, B.u.z,
-                                B.e2, hx2, hy, E2);
-        const float q3 = q_node(C.pt.w, C.s.w, C.e3, C.u.z, C.e2, C.uR, C.eR, A.u.w, A.e3, B.u.w,
-                                B.e3, hx3, hy, E3);
-        if (!PASS2) {
-          // <phat, qhat>: terms pt*q 2^-(e+E); align to the largest scale
-          acc_add(acc, C.pt.x * q0, -(C.e0 + E0));
-          acc_add(acc, C.pt.y * q1, -(C.e1 + E1));
-          acc_add(acc, C.pt.z * q2, -(C.e2 + E2));
-          acc_add(acc, C.pt.w * q3, -(C.e3 + E3));
-        } else {
-          const int64_t o = (int64_t)y * g.nx + x;
-          const int ki = kx[(x >> cg.lgB) + cg.cx * (y >> cg.lgB)];
-          float4 d = ld4(d32 + o);
-          float rn[4], pn[4];
-          int en[4];
-          const float pts[4] = {C.pt.x, C.pt.y, C.pt.z, C.pt.w};
-          const float rs[4] = {C.r.x, C.r.y, C.r.z, C.r.w};
-          const float qs[4] = {q0, q1, q2, q3};
-          const int es[4] = {C.e0, C.e1, C.e2, C.e3};
-          const int Es[4] = {E0, E1, E2, E3};
-          float dd[4] = {d.x, d.y, d.z, d.w};
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            if (pts[j] != 0.f) dd[j] = fmaf(alpha * pts[j], pow2f(ki - es[j]), dd[j]);
-            const float f = pow2f(Es[j] - es[j]);
-            const float rE = fmaf(-alpha, qs[j], rs[j] * f);
-            const float pE = pts[j] * f;
-            const float mx = fmaxf(fabsf(rE), fabsf(pE));
-            if (mx > 0.f && mx <= 3.4e38f) {
-              const int sh = expof(mx);
-              const float sc = pow2f(-sh);
-              rn[j] = rE * sc;
-              pn[j] = pE * sc;
-              en[j] = Es[j] - sh;
-            } else {
-              rn[j] = 0.f;
-              pn[j] = 0.f;
-              en[j] = kNoExp;
-              if (!(mx <= 3.4e38f)) rmax = INFINITY;
-            }
-          }
-          // <rhat, rhat> terms rn^2 2^-2en
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc_add(acc, rn[j] * rn[j], -2 * en[j]);
-          float4 xr = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (mode != 0) xr = ld4(xref + o);
-          const float xrs[4] = {xr.x, xr.y, xr.z, xr.w};
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            if (rn[j] == 0.f) continue;
-            const float rk = fabsf(rn[j]) * pow2f(ki - en[j]);
-            if (mode == 0)
-              rmax = fmaxf(rmax, rk);
-            else if (rk > theta * fabsf(xrs[j] + dd[j]))
-              rmax = 1.f;
-          }
-          *reinterpret_cast<float4 *>(d32 + o) = make_float4(dd[0], dd[1], dd[2], dd[3]);
-          *reinterpret_cast<float4 *>(r32o + o) = make_float4(rn[0], rn[1], rn[2], rn[3]);
-          *reinterpret_cast<float4 *>(p32o + o) = make_float4(pn[0], pn[1], pn[2], pn[3]);
-          uint2 ev;
-          ev.x = (uint32_t)(uint16_t)(short)max(-32000, min(en[0], 32000)) |
-                 ((uint32_t)(uint16_t)(short)max(-32000, min(en[1], 32000)) << 16);
-          ev.y = (uint32_t)(uint16_t)(short)max(-32000, min(en[2], 32000)) |
-                 ((uint32_t)(uint16_t)(short)max(-32000, min(en[3], 32000)) << 16);
-          *reinterpret_cast<uint2 *>(e16o + o) = ev;
-        }
-      }
-      A = C;
-      C = B;
-    }
-  }
   const Acc64 tot = block_acc(to64(acc), shm, shs);
   float bm = 0.f;
   if (PASS2) bm = block_maxf(rmax, shf);
@@ -891,7 +831,11 @@ k_mixed2d(Grid g, CellGrid cg, int tiles_x, int ntiles, const int *__restrict__ 
   if (!PASS2) {
     if (threadIdx.x == 0) {
       const Acc64 rho{st->rho_m, st->rho_s};
-      if (sum.m > 0.0 && isfinite(sum.m)) {
+      if (st->fault) {
+        st->alpha = 0.0;
+        st->done = 1;
+        st->status = EIK_ERR_TIMEOUT;
+      } else if (sum.m > 0.0 && isfinite(sum.m)) {
         st->alpha = acc_ratio(rho, sum);
       } else if (rho.m == 0.0) {
         st->alpha = 0.0;
@@ -913,7 +857,10 @@ k_mixed2d(Grid g, CellGrid cg, int tiles_x, int ntiles, const int *__restrict__ 
       st->rho_s = sum.s;
       st->iter += 1;
       st->total_iter += 1;
-      if (!isfinite(sum.m) || !isfinite(st->beta)) {
+      if (st->fault) {
+        st->done = 1;
+        st->status = EIK_ERR_TIMEOUT;
+      } else if (!isfinite(sum.m) || !isfinite(st->beta)) {
         st->done = 1;
         st->status = EIK_ERR_BREAKDOWN;
       } else if ((st->mode == 0 ? rm <= (double)st->thresh : rm == 0.0) || sum.m == 0.0) {
@@ -926,6 +873,412 @@ k_mixed2d(Grid g, CellGrid cg, int tiles_x, int ntiles, const int *__restrict__ 
       st->counter[2] = 0u;
     }
   }
+}
+
+template <bool PASS2, int VEC>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+k_mixed2d(Grid g, CellGrid cg, int tiles_x, int ntiles, const int *__restrict__ kx,
+          const float *__restrict__ r32, const float *__restrict__ p32,
+          const short *__restrict__ e16, const float *__restrict__ s32,
+          float *__restrict__ r32o, float *__restrict__ p32o, short *__restrict__ e16o,
+          float *__restrict__ d32, const float *__restrict__ xref, MixState *st, double *part,
+          int nblk_part) {
+  constexpr int W = 32 * VEC;   // columns per warp
+  if (st->done) return;
+  const float beta = (float)st->beta, alpha = (float)st->alpha;
+  const int mode = st->mode;
+  const float theta = st->theta;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool half = g.boundary == EIK_BOUNDARY_HALF_CELL;
+  Acc32 acc{0.f, 0};
+  float rmax = 0.f;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int xw = (t % tiles_x) * W;
+    const int x = xw + VEC * lane;
+    const int y0 = (t / tiles_x) * kRowTile + warp * kRowsPerWarp;
+    if (y0 >= g.ny) continue;   // whole warp: uniform
+    // face weights of the columns (x edges carry hy, y edges hx)
+    float hx[VEC];
+#pragma unroll
+    for (int j = 0; j < VEC; ++j)
+      hx[j] = (half && (x + j == 0 || x + j == g.nx - 1)) ? 0.5f : 1.f;
+    Row<VEC> A, C, B;   // above, current, below
+    load_row<VEC>(g, x, xw, y0 - 1, beta, r32, p32, e16, s32, A);
+    load_row<VEC>(g, x, xw, y0, beta, r32, p32, e16, s32, C);
+    for (int k = 0; k < kRowsPerWarp; ++k) {
+      const int y = y0 + k;
+      load_row<VEC>(g, x, xw, y + 1, beta, r32, p32, e16, s32, B);
+      if (y < g.ny && x < g.nx) {
+        const float hy = (half && (y == 0 || y == g.ny - 1)) ? 0.5f : 1.f;
+        float q[VEC];
+        int E[VEC];
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) {
+          const float uL = (j == 0) ? C.uL : C.u[j - 1];
+          const int eL = (j == 0) ? C.eL : C.e[j - 1];
+          const float uR = (j == VEC - 1) ? C.uR : C.u[j + 1];
+          const int eR = (j == VEC - 1) ? C.eR : C.e[j + 1];
+          q[j] = q_node(C.pt[j], C.s[j], C.e[j], uL, eL, uR, eR, A.u[j], A.e[j], B.u[j], B.e[j],
+                        hx[j], hy, E[j]);
+        }
+        if (!PASS2) {
+          // <phat, qhat>: terms pt*q 2^-(e+E)
+#pragma unroll
+          for (int j = 0; j < VEC; ++j) acc_add(acc, C.pt[j] * q[j], -(C.e[j] + E[j]));
+        } else {
+          const int64_t o = (int64_t)y * g.nx + x;
+          const int ki = kx[(x >> cg.lgB) + cg.cx * (y >> cg.lgB)];
+          float dd[VEC], rn[VEC], pn[VEC], xr[VEC];
+          int en[VEC];
+          ldv<VEC>(d32 + o, dd);
+#pragma unroll
+          for (int j = 0; j < VEC; ++j) {
+            const float pt = C.pt[j];
+            if (pt != 0.f) dd[j] = fmaf(alpha * pt, pow2f(ki - C.e[j]), dd[j]);
+            const float f = pow2f(E[j] - C.e[j]);
+            const float rE = fmaf(-alpha, q[j], C.r[j] * f);
+            const float pE = pt * f;
+            const float mx = fmaxf(fabsf(rE), fabsf(pE));
+            if (mx > 0.f && mx <= 3.4e38f) {
+              const int sh = expof(mx);
+              const float sc = pow2f(-sh);
+              rn[j] = rE * sc;
+              pn[j] = pE * sc;
+              en[j] = E[j] - sh;
+            } else {
+              rn[j] = 0.f;
+              pn[j] = 0.f;
+              en[j] = kNoExp;
+              if (!(mx <= 3.4e38f)) rmax = INFINITY;
+            }
+            acc_add(acc, rn[j] * rn[j], -2 * en[j]);   // <rhat, rhat>
+          }
+          if (mode != 0) ldv<VEC>(xref + o, xr);
+#pragma unroll
+          for (int j = 0; j < VEC; ++j) {
+            if (rn[j] == 0.f) continue;
+            const float rk = fabsf(rn[j]) * pow2f(ki - en[j]);
+            if (mode == 0)
+              rmax = fmaxf(rmax, rk);
+            else if (rk > theta * fabsf(xr[j] + dd[j]))
+              rmax = 1.f;
+          }
+          stv<VEC>(d32 + o, dd);
+          stv<VEC>(r32o + o, rn);
+          stv<VEC>(p32o + o, pn);
+          ste<VEC>(e16o + o, en);
+        }
+      }
+      A = C;
+      C = B;
+    }
+  }
+  inner_pass_tail<PASS2>(acc, rmax, st, part, nblk_part);
+}
+
+// ------------------------------------ 2D inner CG, TMA-staged tiles (sm_103a)
+// A block owns tiles of kTmaTX x TY nodes.  For each tile one thread issues
+// tensor-memory-accelerator copies of r, p, sigma and e with a one-node halo
+// (and, in pass 2, of d and xref without halo) into a shared-memory stage and
+// the block waits on that stage's mbarrier; two stages alternate, so the
+// copies of the next tile are in flight while the current one is computed.
+// Every copy lands whole: nothing on the data path waits on a single global
+// load.  Inside a tile a warp owns 64 columns (2 per lane) and marches down
+// TY/RG rows, computing u = sigma (r + beta p) of each row once and taking
+// the x neighbours by warp shuffle.  The arithmetic per node is that of
+// q_node / k_mixed2d above.
+//
+// Requirements (checked on the host): 2D, nx a multiple of 8 (the row pitch
+// of the int16 exponents must be a multiple of 16 bytes).  Nodes outside the
+// grid arrive as zeros (TMA fill); a neighbour with u = 0 is left out of the
+// exponent minimum, so the zero fill needs no special case.
+constexpr int kTmaTX = 128;                 // tile columns
+constexpr int kTmaStages = 2;
+constexpr unsigned long long kTmaWaitNs = 200ull * 1000 * 1000;   // 0.2 s
+
+template <int TY>
+struct TmaTile {
+  static constexpr int H = TY + 2;                         // rows incl. halo
+  static constexpr int FW = kTmaTX + 8;                    // floats: x0-4 .. x0+TX+3
+  static constexpr int EW = kTmaTX + 16;                   // shorts: x0-8 .. x0+TX+7
+  static constexpr int F_BYTES = ((FW * H * 4 + 127) / 128) * 128;
+  static constexpr int E_BYTES = ((EW * H * 2 + 127) / 128) * 128;
+  static constexpr int C_BYTES = kTmaTX * TY * 4;          // d / xref tiles (no halo)
+  static constexpr int OFF_R = 0, OFF_P = F_BYTES, OFF_S = 2 * F_BYTES;
+  static constexpr int OFF_E = 3 * F_BYTES;
+  static constexpr int OFF_D = OFF_E + E_BYTES, OFF_X = OFF_D + C_BYTES;
+  static constexpr int STAGE1 = OFF_D;                     // pass 1 stage bytes
+  static constexpr int STAGE2 = OFF_X + C_BYTES;           // pass 2 stage bytes
+  static constexpr int smem(bool pass2) { return kTmaStages * (pass2 ? STAGE2 : STAGE1) + 128; }
+};
+
+struct TmaMaps {
+  CUtensorMap r, p, e;   // one buffer set (halo boxes)
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for phase `parity` of the barrier for at most kTmaWaitNs.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *b, uint32_t parity) {
+  if (mbar_try_wait(b, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    if (mbar_try_wait(b, parity)) return true;
+    if (global_ns() - t0 > kTmaWaitNs) return false;
+  }
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                            uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// One TMA row of the tile, as seen by one lane (2 columns).
+struct TRow {
+  float r0, r1, pt0, pt1, s0, s1, u0, u1;
+  int e0, e1;    // stored exponents (centre use)
+  int n0, n1;    // exponents for neighbour use: kNoExp where u == 0
+};
+
+template <int TY>
+__device__ __forceinline__ void trow_load(const unsigned char *stage, int j, int lc, float beta,
+                                          TRow &R) {
+  using T = TmaTile<TY>;
+  const float *sr = reinterpret_cast<const float *>(stage + T::OFF_R);
+  const float *sp = reinterpret_cast<const float *>(stage + T::OFF_P);
+  const float *ss = reinterpret_cast<const float *>(stage + T::OFF_S);
+  const short *se = reinterpret_cast<const short *>(stage + T::OFF_E);
+  const int fo = j * T::FW + lc + 4, eo = j * T::EW + lc + 8;
+  const float2 r = *reinterpret_cast<const float2 *>(sr + fo);
+  const float2 p = *reinterpret_cast<const float2 *>(sp + fo);
+  const float2 sg = *reinterpret_cast<const float2 *>(ss + fo);
+  const unsigned int ee = *reinterpret_cast<const unsigned int *>(se + eo);
+  R.r0 = r.x;
+  R.r1 = r.y;
+  R.pt0 = fmaf(beta, p.x, r.x);
+  R.pt1 = fmaf(beta, p.y, r.y);
+  R.s0 = sg.x;
+  R.s1 = sg.y;
+  R.u0 = sg.x * R.pt0;
+  R.u1 = sg.y * R.pt1;
+  R.e0 = (short)(ee & 0xffffu);
+  R.e1 = (short)(ee >> 16);
+  R.n0 = (R.u0 != 0.f) ? R.e0 : kNoExp;
+  R.n1 = (R.u1 != 0.f) ? R.e1 : kNoExp;
+}
+
+// u and neighbour exponent of a single tile-local column c of smem row j.
+template <int TY>
+__device__ __forceinline__ void tcol_load(const unsigned char *stage, int j, int c, float beta,
+                                          float &u, int &n) {
+  using T = TmaTile<TY>;
+  const float *sr = reinterpret_cast<const float *>(stage + T::OFF_R);
+  const float *sp = reinterpret_cast<const float *>(stage + T::OFF_P);
+  const float *ss = reinterpret_cast<const float *>(stage + T::OFF_S);
+  const short *se = reinterpret_cast<const short *>(stage + T::OFF_E);
+  const int fo = j * T::FW + c + 4;
+  u = ss[fo] * fmaf(beta, sp[fo], sr[fo]);
+  n = (u != 0.f) ? (int)se[j * T::EW + c + 8] : kNoExp;
+}
+
+template <bool PASS2, int TY, int RG>
+__global__ void __launch_bounds__(64 * RG, 1)
+k_mixed2d_tma(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtensorMap tm_p,
+              const __grid_constant__ CUtensorMap tm_e, const __grid_constant__ CUtensorMap tm_s,
+              const __grid_constant__ CUtensorMap tm_d, const __grid_constant__ CUtensorMap tm_x,
+              Grid g, CellGrid cg, int tiles_x, int ntiles, const int *__restrict__ kx,
+              float *__restrict__ r32o, float *__restrict__ p32o, short *__restrict__ e16o,
+              float *__restrict__ d32, MixState *st, double *part, int nblk_part) {
+  using T = TmaTile<TY>;
+  constexpr int RW = TY / RG;   // rows marched by one warp
+  static_assert(TY % RG == 0, "rows per warp");
+  extern __shared__ unsigned char tma_smem_raw[];
+  __shared__ __align__(8) uint64_t bar[kTmaStages];
+  if (st->done) return;
+  unsigned char *smem = reinterpret_cast<unsigned char *>(
+      (reinterpret_cast<uintptr_t>(tma_smem_raw) + 127) & ~uintptr_t(127));
+  constexpr int STAGE = PASS2 ? T::STAGE2 : T::STAGE1;
+  const float beta = (float)st->beta, alpha = (float)st->alpha;
+  const int mode = st->mode;
+  const float theta = st->theta;
+  const bool want_x = PASS2 && mode != 0;
+  const uint32_t tx_bytes =
+      3 * (T::FW * T::H * 4) + T::EW * T::H * 2 + (PASS2 ? T::C_BYTES : 0) +
+      (want_x ? T::C_BYTES : 0);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int cw = warp & 1, rg = warp >> 1;
+  const bool half = g.boundary == EIK_BOUNDARY_HALF_CELL;
+
+  auto issue = [&](int t, int stg) {
+    unsigned char *dst = smem + stg * STAGE;
+    const int x0 = (t % tiles_x) * kTmaTX, y0 = (t / tiles_x) * TY;
+    mbar_expect_tx(&bar[stg], tx_bytes);
+    tma_load_2d(dst + T::OFF_R, &tm_r, x0 - 4, y0 - 1, &bar[stg]);
+    tma_load_2d(dst + T::OFF_P, &tm_p, x0 - 4, y0 - 1, &bar[stg]);
+    tma_load_2d(dst + T::OFF_S, &tm_s, x0 - 4, y0 - 1, &bar[stg]);
+    tma_load_2d(dst + T::OFF_E, &tm_e, x0 - 8, y0 - 1, &bar[stg]);
+    if (PASS2) tma_load_2d(dst + T::OFF_D, &tm_d, x0, y0, &bar[stg]);
+    if (want_x) tma_load_2d(dst + T::OFF_X, &tm_x, x0, y0, &bar[stg]);
+  };
+
+  if (tid == 0) {
+    for (int k = 0; k < kTmaStages; ++k) mbar_init(&bar[k], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  const int first = blockIdx.x, step = gridDim.x;
+  if (tid == 0)
+    for (int k = 0; k < kTmaStages; ++k)
+      if (first + k * step < ntiles) issue(first + k * step, k);
+
+  Acc32 acc{0.f, 0};
+  float rmax = 0.f;
+  bool fault = false;
+  int k = 0;
+  for (int t = first; t < ntiles; t += step, ++k) {
+    const int stg = k % kTmaStages;
+    const uint32_t parity = (uint32_t)(k / kTmaStages) & 1u;
+    const bool ok = mbar_wait_bounded(&bar[stg], parity);
+    if (__syncthreads_or(!ok)) {
+      fault = true;
+      break;
+    }
+    const unsigned char *S = smem + stg * STAGE;
+    const int x0 = (t % tiles_x) * kTmaTX, y0 = (t / tiles_x) * TY;
+    const int lc = 64 * cw + 2 * lane;          // tile-local column of node 0
+    const int x = x0 + lc;
+    const int hc = (lane == 0) ? lc - 1 : lc + 2;   // halo column (lanes 0, 31)
+    const float hx0 = (half && x == 0) ? 0.5f : 1.f;
+    const float hx1 = (half && x + 1 == g.nx - 1) ? 0.5f : 1.f;
+    TRow A, C, B;
+    const int j0 = rg * RW + 1;                 // smem row of the first centre row
+    trow_load<TY>(S, j0 - 1, lc, beta, A);
+    trow_load<TY>(S, j0, lc, beta, C);
+#pragma unroll 2
+    for (int i = 0; i < RW; ++i) {
+      const int j = j0 + i;
+      const int y = y0 + j - 1;
+      trow_load<TY>(S, j + 1, lc, beta, B);
+      float uh = 0.f;
+      int nh = kNoExp;
+      if (lane == 0 || lane == 31) tcol_load<TY>(S, j, hc, beta, uh, nh);
+      float uL = __shfl_up_sync(0xffffffffu, C.u1, 1);
+      int nL = __shfl_up_sync(0xffffffffu, C.n1, 1);
+      float uR = __shfl_down_sync(0xffffffffu, C.u0, 1);
+      int nR = __shfl_down_sync(0xffffffffu, C.n0, 1);
+      if (lane == 0) {
+        uL = uh;
+        nL = nh;
+      }
+      if (lane == 31) {
+        uR = uh;
+        nR = nh;
+      }
+      if (y < g.ny && x < g.nx) {
+        const float hy = (half && (y == 0 || y == g.ny - 1)) ? 0.5f : 1.f;
+        int E0, E1;
+        const float q0 = q_node(C.pt0, C.s0, C.e0, uL, nL, C.u1, C.n1, A.u0, A.n0, B.u0, B.n0,
+                                hx0, hy, E0);
+        const float q1 = q_node(C.pt1, C.s1, C.e1, C.u0, C.n0, uR, nR, A.u1, A.n1, B.u1, B.n1,
+                                hx1, hy, E1);
+        if (!PASS2) {
+          acc_add(acc, C.pt0 * q0, -(C.e0 + E0));
+          acc_add(acc, C.pt1 * q1, -(C.e1 + E1));
+        } else {
+          const int li = (j - 1) * kTmaTX + lc;   // tile-local index, no halo
+          const float2 dd = *reinterpret_cast<const float2 *>(S + T::OFF_D + 4 * li);
+          float2 xr = make_float2(0.f, 0.f);
+          if (want_x) xr = *reinterpret_cast<const float2 *>(S + T::OFF_X + 4 * li);
+          const int kyi = kx[(x >> cg.lgB) + cg.cx * (y >> cg.lgB)];   // x, x+1: one cell
+          float d[2] = {dd.x, dd.y}, rn[2], pn[2];
+          int en[2];
+          const float pt[2] = {C.pt0, C.pt1}, rr[2] = {C.r0, C.r1}, q[2] = {q0, q1};
+          const int ee[2] = {C.e0, C.e1}, EE[2] = {E0, E1};
+          const float xx[2] = {xr.x, xr.y};
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            if (pt[c] != 0.f) d[c] = fmaf(alpha * pt[c], pow2f(kyi - ee[c]), d[c]);
+            const float f = pow2f(EE[c] - ee[c]);
+            const float rE = fmaf(-alpha, q[c], rr[c] * f);
+            const float pE = pt[c] * f;
+            const float mx = fmaxf(fabsf(rE), fabsf(pE));
+            if (mx > 0.f && mx <= 3.4e38f) {
+              const int sh = expof(mx);
+              const float sc = pow2f(-sh);
+              rn[c] = rE * sc;
+              pn[c] = pE * sc;
+              en[c] = EE[c] - sh;
+              acc_add(acc, rn[c] * rn[c], -2 * en[c]);
+              const float rk = fabsf(rn[c]) * pow2f(kyi - en[c]);
+              if (mode == 0)
+                rmax = fmaxf(rmax, rk);
+              else if (rk > theta * fabsf(xx[c] + d[c]))
+                rmax = 1.f;
+            } else {
+              rn[c] = 0.f;
+              pn[c] = 0.f;
+              en[c] = kNoExp;
+              if (!(mx <= 3.4e38f)) rmax = INFINITY;
+            }
+          }
+          const int64_t o = (int64_t)y * g.nx + x;
+          *reinterpret_cast<float2 *>(d32 + o) = make_float2(d[0], d[1]);
+          *reinterpret_cast<float2 *>(r32o + o) = make_float2(rn[0], rn[1]);
+          *reinterpret_cast<float2 *>(p32o + o) = make_float2(pn[0], pn[1]);
+          *reinterpret_cast<unsigned int *>(e16o + o) = pack2(en[0], en[1]);
+        }
+      }
+      A = C;
+      C = B;
+    }
+    __syncthreads();   // every thread is done with this stage
+    if (tid == 0 && t + kTmaStages * step < ntiles) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(t + kTmaStages * step, stg);
+    }
+  }
+  if (fault) {
+    // leave no copy in flight: wait (bounded) for every stage still pending
+    if (tid == 0) {
+      atomicExch(&st->fault, 1);
+      for (int kk = k; kk < k + kTmaStages; ++kk) {
+        const int t = first + kk * step;
+        if (t >= ntiles) break;
+        mbar_wait_bounded(&bar[kk % kTmaStages], (uint32_t)(kk / kTmaStages) & 1u);
+      }
+    }
+    __syncthreads();
+  }
+  inner_pass_tail<PASS2>(acc, rmax, st, part, nblk_part);
 }
 
 // x64 += d (kx units, unknowns only: d is zero on the sources).
@@ -978,8 +1331,12 @@ struct MixedState {
   TileCount tc;
   CellGrid cg;
   int nblk_stencil = 0, nblk_part = 0, cap = 0;
-  bool rows2d = false;           // warp-marched 2D kernels (nx % 4 == 0)
+  bool rows2d = false;           // warp-marched 2D kernels (nx % vec == 0)
+  int vec = 2;                   // columns per lane
   int tiles_x = 0, ntiles2d = 0, nblk2d = 0;
+  int tma = 0;                   // TMA-staged 2D kernels: variant index (0 = off)
+  int tma_tiles_x = 0, tma_ntiles = 0, tma_nblk1 = 0, tma_nblk2 = 0;
+  CUtensorMap tm_r[2], tm_p[2], tm_e[2], tm_s, tm_d, tm_x;
   float *s32 = nullptr, *fb = nullptr, *St = nullptr, *d32 = nullptr, *xref = nullptr;
   float *r32[2] = {nullptr, nullptr}, *p32[2] = {nullptr, nullptr};
   short *e16[2] = {nullptr, nullptr};
@@ -1037,6 +1394,96 @@ const char *mixed_last_error() { return g_msg.c_str(); }
     }                                                                    \
   } while (0)
 
+// TMA variants: (rows per tile, row groups per block); 2 warps per row
+// group.  Variant 3 (16 rows, 8 warps) is the library default: it measured
+// fastest on the 2048^2 workload.
+constexpr int kTmaVariantCount = 4;
+constexpr int kTmaTYs[kTmaVariantCount] = {16, 32, 16, 32};   // row groups: 2, 4, 4, 2
+
+template <int TY, int RG>
+static bool tma_setup_t(MixedState *m, int num_sms) {
+  using T = TmaTile<TY>;
+  const int s1 = T::smem(false), s2 = T::smem(true);
+  if (cudaFuncSetAttribute(k_mixed2d_tma<false, TY, RG>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, s1) != cudaSuccess ||
+      cudaFuncSetAttribute(k_mixed2d_tma<true, TY, RG>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, s2) != cudaSuccess)
+    return false;
+  int per1 = 0, per2 = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, k_mixed2d_tma<false, TY, RG>, 64 * RG,
+                                                    s1) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_mixed2d_tma<true, TY, RG>, 64 * RG,
+                                                    s2) != cudaSuccess)
+    return false;
+  if (per1 < 1 || per2 < 1) return false;
+  m->tma_tiles_x = (m->g.nx + kTmaTX - 1) / kTmaTX;
+  m->tma_ntiles = m->tma_tiles_x * ((m->g.ny + TY - 1) / TY);
+  m->tma_nblk1 = std::min(m->tma_ntiles, per1 * num_sms);
+  m->tma_nblk2 = std::min(m->tma_ntiles, per2 * num_sms);
+  return true;
+}
+
+static bool tma_setup(MixedState *m, int v, int num_sms) {
+  m->tma = v;
+  switch (v) {
+    case 1: return tma_setup_t<16, 2>(m, num_sms);
+    case 2: return tma_setup_t<32, 4>(m, num_sms);
+    case 3: return tma_setup_t<16, 4>(m, num_sms);
+    case 4: return tma_setup_t<32, 2>(m, num_sms);
+  }
+  return false;
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return (EncodeTiledFn) nullptr;
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+// 2D tiled tensor map over an nx x ny row-major array; box bw x bh elements.
+static bool encode_2d(CUtensorMap *map, void *base, bool is_short, int nx, int ny, int bw,
+                      int bh) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  const size_t es = is_short ? 2 : 4;
+  const cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
+  const cuuint64_t strides[1] = {(cuuint64_t)nx * es};
+  const cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(map, is_short ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+            base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static bool tma_encode(MixedState *m) {
+  const int ty = kTmaTYs[m->tma - 1];
+  const int nx = m->g.nx, ny = m->g.ny;
+  const int fw = kTmaTX + 8, ew = kTmaTX + 16, h = ty + 2;
+  bool ok = true;
+  for (int k = 0; k < 2; ++k) {
+    ok = ok && encode_2d(&m->tm_r[k], m->r32[k], false, nx, ny, fw, h);
+    ok = ok && encode_2d(&m->tm_p[k], m->p32[k], false, nx, ny, fw, h);
+    ok = ok && encode_2d(&m->tm_e[k], m->e16[k], true, nx, ny, ew, h);
+  }
+  ok = ok && encode_2d(&m->tm_s, m->s32, false, nx, ny, fw, h);
+  ok = ok && encode_2d(&m->tm_d, m->d32, false, nx, ny, kTmaTX, ty);
+  ok = ok && encode_2d(&m->tm_x, m->xref, false, nx, ny, kTmaTX, ty);
+  return ok;
+}
+
 template <class T>
 static bool mal(T **p, size_t n) {
   return cudaMalloc((void **)p, sizeof(T) * (n ? n : 1)) == cudaSuccess;
@@ -1071,17 +1518,37 @@ eik_status mixed_create(MixedState **out, const Grid &g, const TileCount &tc, in
   if (per_sm < 1) per_sm = 1;
   m->nblk_stencil = (int)std::min<int64_t>(tc.total, (int64_t)per_sm * num_sms);
   m->cap = num_sms * 8;
-  // tile_override == 1 selects the generic halo-tile kernels everywhere
-  if (g.ndim == 2 && g.nx % 4 == 0 && tile_override != 1) {
+  // tile_override: 0 library choice, 1 generic halo tiles, 2 / 3 warp-marched
+  // rows with 4 / 2 columns per lane, 4..7 TMA-staged tiles (variants 1..4
+  // listed at kTmaTYs)
+  const int vec = (tile_override == 2) ? 4 : 2;
+  const bool tma_ok = g.ndim == 2 && g.nx % 8 == 0 && (tile_override == 0 || tile_override >= 4);
+  const bool march_ok = g.ndim == 2 && g.nx % vec == 0 &&
+                        (tile_override == 0 || tile_override == 2 || tile_override == 3);
+  if (march_ok) {
     int per = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mixed2d<true>, kWarpsPerBlock * 32, 0);
+    if (vec == 4)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mixed2d<true, 4>, kWarpsPerBlock * 32, 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mixed2d<true, 2>, kWarpsPerBlock * 32, 0);
     if (per < 1) per = 1;
     m->rows2d = true;
-    m->tiles_x = (g.nx + 127) / 128;
+    m->vec = vec;
+    m->tiles_x = (g.nx + 32 * vec - 1) / (32 * vec);
     m->ntiles2d = m->tiles_x * ((g.ny + kRowTile - 1) / kRowTile);
     m->nblk2d = std::min(m->ntiles2d, per * num_sms);
   }
+  if (tma_ok) {
+    const int v = (tile_override >= 4) ? tile_override - 3 : 3;   // default: 16 rows, 8 warps
+    if (v <= kTmaVariantCount && tma_setup(m, v, num_sms)) {
+      m->rows2d = false;
+    } else {
+      m->tma = 0;
+      cudaGetLastError();
+    }
+  }
   m->nblk_part = std::max(std::max(m->nblk_stencil, m->cap), m->nblk2d);
+  m->nblk_part = std::max(m->nblk_part, std::max(m->tma_nblk1, m->tma_nblk2));
   const int64_t n = g.n;
   bool ok = mal(&m->s32, n) && mal(&m->d32, n) && mal(&m->xref, n) && mal(&m->r32[0], n) && mal(&m->r32[1], n) &&
             mal(&m->p32[0], n) && mal(&m->p32[1], n) && mal(&m->e16[0], n) &&
@@ -1095,7 +1562,14 @@ eik_status mixed_create(MixedState **out, const Grid &g, const TileCount &tc, in
     g_msg = "device allocation failed";
     return EIK_ERR_OOM;
   }
-  const size_t smem = 2 * sizeof(float) * m->cg.ncell;
+  if (m->tma && !tma_encode(m)) {
+    mixed_destroy(m);
+    g_msg = "cannot encode the TMA tensor maps";
+    return EIK_ERR_CUDA;
+  }
+  // the attribute belongs to the function, not to this solver: set it to the
+  // largest cell grid any solver can use, so concurrent solvers agree
+  const size_t smem = 2 * sizeof(float) * kMaxCells;
   if (cudaFuncSetAttribute(k_coarse_exponents, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess) {
     cudaGetLastError();
@@ -1137,16 +1611,48 @@ static void launch_iteration(MixedState *m, int set, cudaStream_t s, bool timed 
   const int a = set, b = 1 - set;
   double *p1 = m->part;
   double *p2 = m->part + 3 * (size_t)m->nblk_part;
+  if (m->tma) {
+#define EIK_LAUNCH_TMA(TY, RG)                                                                  \
+  do {                                                                                          \
+    if (timed) cudaEventRecord(m->ev[0], s);                                                    \
+    k_mixed2d_tma<false, TY, RG><<<m->tma_nblk1, 64 * RG, TmaTile<TY>::smem(false), s>>>(       \
+        m->tm_r[a], m->tm_p[a], m->tm_e[a], m->tm_s, m->tm_d, m->tm_x, m->g, m->cg,             \
+        m->tma_tiles_x, m->tma_ntiles, m->kx, nullptr, nullptr, nullptr, m->d32, m->st, p1,     \
+        m->nblk_part);                                                                          \
+    if (timed) cudaEventRecord(m->ev[1], s);                                                    \
+    k_mixed2d_tma<true, TY, RG><<<m->tma_nblk2, 64 * RG, TmaTile<TY>::smem(true), s>>>(         \
+        m->tm_r[a], m->tm_p[a], m->tm_e[a], m->tm_s, m->tm_d, m->tm_x, m->g, m->cg,             \
+        m->tma_tiles_x, m->tma_ntiles, m->kx, m->r32[b], m->p32[b], m->e16[b], m->d32, m->st,   \
+        p2, m->nblk_part);                                                                      \
+    if (timed) cudaEventRecord(m->ev[2], s);                                                    \
+  } while (0)
+    switch (m->tma) {
+      case 1: EIK_LAUNCH_TMA(16, 2); break;
+      case 2: EIK_LAUNCH_TMA(32, 4); break;
+      case 3: EIK_LAUNCH_TMA(16, 4); break;
+      default: EIK_LAUNCH_TMA(32, 2); break;
+    }
+#undef EIK_LAUNCH_TMA
+    return;
+  }
   if (m->rows2d) {
-    if (timed) cudaEventRecord(m->ev[0], s);
-    k_mixed2d<false><<<m->nblk2d, kWarpsPerBlock * 32, 0, s>>>(
-        m->g, m->cg, m->tiles_x, m->ntiles2d, m->kx, m->r32[a], m->p32[a], m->e16[a], m->s32,
-        nullptr, nullptr, nullptr, m->d32, m->xref, m->st, p1, m->nblk_part);
-    if (timed) cudaEventRecord(m->ev[1], s);
-    k_mixed2d<true><<<m->nblk2d, kWarpsPerBlock * 32, 0, s>>>(
-        m->g, m->cg, m->tiles_x, m->ntiles2d, m->kx, m->r32[a], m->p32[a], m->e16[a], m->s32,
-        m->r32[b], m->p32[b], m->e16[b], m->d32, m->xref, m->st, p2, m->nblk_part);
-    if (timed) cudaEventRecord(m->ev[2], s);
+#define EIK_LAUNCH_2D(V)                                                                        \
+  do {                                                                                          \
+    if (timed) cudaEventRecord(m->ev[0], s);                                                    \
+    k_mixed2d<false, V><<<m->nblk2d, kWarpsPerBlock * 32, 0, s>>>(                              \
+        m->g, m->cg, m->tiles_x, m->ntiles2d, m->kx, m->r32[a], m->p32[a], m->e16[a], m->s32,   \
+        nullptr, nullptr, nullptr, m->d32, m->xref, m->st, p1, m->nblk_part);                   \
+    if (timed) cudaEventRecord(m->ev[1], s);                                                    \
+    k_mixed2d<true, V><<<m->nblk2d, kWarpsPerBlock * 32, 0, s>>>(                               \
+        m->g, m->cg, m->tiles_x, m->ntiles2d, m->kx, m->r32[a], m->p32[a], m->e16[a], m->s32,   \
+        m->r32[b], m->p32[b], m->e16[b], m->d32, m->xref, m->st, p2, m->nblk_part);             \
+    if (timed) cudaEventRecord(m->ev[2], s);                                                    \
+  } while (0)
+    if (m->vec == 4)
+      EIK_LAUNCH_2D(4);
+    else
+      EIK_LAUNCH_2D(2);
+#undef EIK_LAUNCH_2D
     return;
   }
   if (timed) cudaEventRecord(m->ev[0], s);
@@ -1207,7 +1713,7 @@ eik_status mixed_solve(MixedState *m, const MixedArgs &a, int *inner_iters, int 
   if (gs != EIK_OK) return gs;
 
   const double tol = a.opt.tol;
-  const double red = (a.opt.inner_tol > 0) ? a.opt.inner_tol : 1e-5;
+  const double red = (a.opt.inner_tol > 0) ? a.opt.inner_tol : 1e-3;
   const int max_outer = (a.opt.max_outer > 0) ? a.opt.max_outer : 30;
   int total = 0, outer = 0;
   double best_cw = INFINITY;
@@ -1292,6 +1798,15 @@ eik_status mixed_solve(MixedState *m, const MixedArgs &a, int *inner_iters, int 
     }
     total += m->h_st->iter;
     ++outer;
+    if (trace)
+      fprintf(stderr, "[mixed]   inner end: iters %d status %d alpha %.3e beta %.3e rho %.3e*2^%d\n",
+              m->h_st->iter, m->h_st->status, m->h_st->alpha, m->h_st->beta, m->h_st->rho_m,
+              m->h_st->rho_s);
+    if (m->h_st->status == EIK_ERR_TIMEOUT) {
+      g_msg = "a device-side wait for a tile copy timed out";
+      result = EIK_ERR_TIMEOUT;
+      break;
+    }
     if (m->h_st->status == EIK_ERR_BREAKDOWN) {
       g_msg = "inner CG breakdown";
       result = EIK_ERR_BREAKDOWN;
