@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--c4-count", type=int, default=256,
                     help="instances in the batched workload (c4)")
     ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--band-bits", type=int, default=0,
+                    help="mixed mode level-set band width (eik_options.band_bits): "
+                         "0 library choice, negative never sweep")
     ap.add_argument("--tile-override", type=int, default=0,
                     help="kernel variant (eik_options.tile_override): 0 library choice, "
                          "1 generic halo tiles, 2 four columns per lane in 2D")
@@ -199,7 +202,8 @@ def run_ours(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
 
     def make(prec):
-        opt = eik.make_options(precision=prec, tol=args.tol, tile_override=args.tile_override)
+        opt = eik.make_options(precision=prec, tol=args.tol, tile_override=args.tile_override,
+                               band_bits=args.band_bits)
         return eik.eik_create(inst.dims, inst.h, inst.hbar, f_dev, src, None, opt)
 
     modes = [args.precision] + [m for m in ("fp64", "mixed") if m != args.precision]
@@ -288,7 +292,7 @@ def run_batch(args):
     insts = wl.config4(count=args.c4_count)
     n_unk = [i.n - len(np.unique(i.src_idx)) for i in insts]
     opt = eik.make_options(precision=args.precision, tol=args.tol,
-                           tile_override=args.tile_override)
+                           tile_override=args.tile_override, band_bits=args.band_bits)
     b = eik.eik_create_batch(insts, opt)
     S = torch.empty(b.n, dtype=torch.float64, device="cuda")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")

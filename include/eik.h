@@ -104,8 +104,15 @@ typedef struct {
   double inner_tol;   /* mixed mode: factor by which the first FP32 inner
                          solve reduces the residual (scaled max norm);
                          0 = library choice (1e-3) */
-  int max_outer;      /* mixed mode: refinement steps; 0 = library choice (30) */
-  int reserved[7];
+  int max_outer;      /* mixed mode: refinement steps (per level-set band);
+                         0 = library choice (30) */
+  int band_bits;      /* mixed mode: when the coarse distance estimate puts
+                         phi over more than 2 * band_bits powers of two, the
+                         solve sweeps level-set bands of band_bits powers of
+                         two (nearest first, half a band of overlap), holding
+                         the rest as Dirichlet data; 0 = library choice (48),
+                         negative = never sweep */
+  int reserved[6];
 } eik_options;
 
 typedef struct {

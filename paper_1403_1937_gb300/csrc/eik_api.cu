@@ -379,6 +379,7 @@ void eik_default_options(eik_options *opt) {
   opt->tile_override = 0;
   opt->inner_tol = 0.0;
   opt->max_outer = 0;
+  opt->band_bits = 0;
 }
 
 const char *eik_last_error(void) { return g_last_error.c_str(); }
@@ -591,8 +592,7 @@ eik_status eik_solve(eik_handle *h, double *S_out, double *phi_out, eik_stats *s
       ma.nsrc = h->nsrc;
       ma.opt = h->opt;
       s = mixed_solve(h->mixed, ma, &iters, &outer, &res_cw, &res_nw);
-      if (s != EIK_OK && s != EIK_ERR_NOT_CONVERGED)
-        g_last_error = mixed_last_error();
+      if (s != EIK_OK) g_last_error = mixed_last_error();
     } else {
       // reset the solution (sources keep their slots)
       CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream));

@@ -29,6 +29,8 @@
 #include <stdio.h>
 #include <stdlib.h>
 
+#include <algorithm>
+#include <climits>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -43,6 +45,8 @@ namespace {
 constexpr int kInnerGraphIters = 32;   // even: the buffer sets alternate
 constexpr int kNoExp = 30000;          // exponent of an all-zero node
 constexpr int kMaxCells = 16384;
+constexpr int kBandBits = 48;          // level-set band width (powers of two of phi)
+constexpr int kMaxSweeps = 3;
 
 thread_local std::string g_msg = "no error";   // per host thread (batches)
 
@@ -175,6 +179,9 @@ struct MixState {
   double cw;         // max |r|/(a phi) over the unknowns
   double r_inf;      // max |rbar64| (kx units)
   double x_inf;      // max |xbar64| (kx units)
+  // level-set band of the refinement step: unknowns in cells with
+  // band_lo <= kx < band_hi take part, all others are held as Dirichlet data
+  int band_lo, band_hi;
 };
 
 struct CellGrid {
@@ -203,6 +210,20 @@ __global__ void k_sig32(int64_t n, const double *__restrict__ sig, float *__rest
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     s32[i] = (float)sig[i];
+}
+
+// s32 for one level-set band: sigma where band_lo <= kx(cell) < band_hi, 0
+// elsewhere (those nodes then act as Dirichlet data in the inner CG).
+__global__ void k_sig32_band(Grid g, CellGrid cg, const int *__restrict__ kx, int lo, int hi,
+                             const double *__restrict__ sig, float *__restrict__ s32) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % g.nx);
+    const int64_t t = i / g.nx;
+    const int y = (int)(t % g.ny), z = (int)(t / g.ny);
+    const int k = kx[cell_of(cg, x, y, z)];
+    s32[i] = (k >= lo && k < hi) ? (float)sig[i] : 0.f;
+  }
 }
 
 // Mean of f over each cell (one block per cell).
@@ -345,6 +366,7 @@ k_mixed_residual(Grid g, TileCount tc, CellGrid cg, const int *__restrict__ kx,
   __shared__ int flag;
   Acc64 rho{0.0, 0};
   double cwm = 0.0, rinf = 0.0, xinf = 0.0;
+  const int band_lo = st->band_lo, band_hi = st->band_hi;
   for (int64_t t = blockIdx.x; t < tc.total; t += gridDim.x) {
     int x0, y0, z0;
     tile_origin_m<DIM>(tc, t, x0, y0, z0);
@@ -372,7 +394,7 @@ k_mixed_residual(Grid g, TileCount tc, CellGrid cg, const int *__restrict__ kx,
       const double si = sig[gi], xi = x64[gi];
       const int ki = sk[s];
       double rb = 0.0;
-      if (si != 0.0) {
+      if (si != 0.0 && ki >= band_lo && ki < band_hi) {
         const double hx = half_if(on_face(gx, g.nx, g.boundary));
         const double hy = half_if(on_face(gy, g.ny, g.boundary));
         double acc;
@@ -875,6 +897,24 @@ __device__ void inner_pass_tail(const Acc32 &acc, float rmax, MixState *st, doub
   }
 }
 
+// 2^n for n <= 0 (0 below the normal range): one clamp and one multiply-add.
+__device__ __forceinline__ float pow2f_le0(int n) {
+  return __int_as_float(max(n, -127) * (1 << 23) + (127 << 23));
+}
+
+// q_node for the TMA kernels: the same value, with the scale factors (all
+// 2^(m - e) with m the minimum exponent, so never above 1) formed by
+// pow2f_le0.
+__device__ __forceinline__ float q_node_le0(float pt, float sg, int ei, float uL, int eL,
+                                            float uR, int eR, float ua, int ea, float ub, int eb,
+                                            float hx, float hy, int &E) {
+  const int m = min(min(ei, min(eL, eR)), min(ea, eb));
+  E = m;
+  const float a1 = uL * pow2f_le0(m - eL) + uR * pow2f_le0(m - eR);
+  const float a2 = ua * pow2f_le0(m - ea) + ub * pow2f_le0(m - eb);
+  return fmaf(-sg, fmaf(hy, a1, hx * a2), pt * pow2f_le0(m - ei));
+}
+
 template <bool PASS2, int VEC>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 k_mixed2d(Grid g, CellGrid cg, int tiles_x, int ntiles, const int *__restrict__ kx,
@@ -1160,7 +1200,11 @@ k_mixed2d_tma(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ 
     for (int k = 0; k < kTmaStages; ++k)
       if (first + k * step < ntiles) issue(first + k * step, k);
 
-  Acc32 acc{0.f, 0};
+  // Inner-product terms are summed in FP32 relative to 2^frame, the scale of
+  // the previous <rhat, rhat>: terms more than 2^126 below it (far-field
+  // nodes with negligible weight) flush to zero, none can overflow.
+  const int frame = st->rho_s;
+  float accf = 0.f;
   float rmax = 0.f;
   bool fault = false;
   int k = 0;
@@ -1206,13 +1250,13 @@ k_mixed2d_tma(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ 
       if (y < g.ny && x < g.nx) {
         const float hy = (half && (y == 0 || y == g.ny - 1)) ? 0.5f : 1.f;
         int E0, E1;
-        const float q0 = q_node(C.pt0, C.s0, C.e0, uL, nL, C.u1, C.n1, A.u0, A.n0, B.u0, B.n0,
-                                hx0, hy, E0);
-        const float q1 = q_node(C.pt1, C.s1, C.e1, C.u0, C.n0, uR, nR, A.u1, A.n1, B.u1, B.n1,
-                                hx1, hy, E1);
+        const float q0 = q_node_le0(C.pt0, C.s0, C.e0, uL, nL, C.u1, C.n1, A.u0, A.n0, B.u0,
+                                    B.n0, hx0, hy, E0);
+        const float q1 = q_node_le0(C.pt1, C.s1, C.e1, C.u0, C.n0, uR, nR, A.u1, A.n1, B.u1,
+                                    B.n1, hx1, hy, E1);
         if (!PASS2) {
-          acc_add(acc, C.pt0 * q0, -(C.e0 + E0));
-          acc_add(acc, C.pt1 * q1, -(C.e1 + E1));
+          accf = fmaf(C.pt0 * q0, pow2f(-(C.e0 + E0) - frame), accf);
+          accf = fmaf(C.pt1 * q1, pow2f(-(C.e1 + E1) - frame), accf);
         } else {
           const int li = (j - 1) * kTmaTX + lc;   // tile-local index, no halo
           const float2 dd = *reinterpret_cast<const float2 *>(S + T::OFF_D + 4 * li);
@@ -1227,17 +1271,17 @@ k_mixed2d_tma(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ 
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
             if (pt[c] != 0.f) d[c] = fmaf(alpha * pt[c], pow2f(kyi - ee[c]), d[c]);
-            const float f = pow2f(EE[c] - ee[c]);
+            const float f = pow2f_le0(EE[c] - ee[c]);
             const float rE = fmaf(-alpha, q[c], rr[c] * f);
             const float pE = pt[c] * f;
             const float mx = fmaxf(fabsf(rE), fabsf(pE));
             if (mx > 0.f && mx <= 3.4e38f) {
               const int sh = expof(mx);
-              const float sc = pow2f(-sh);
+              const float sc = __int_as_float((127 - sh) << 23);   // 2^-sh, sh in [-127, 127]
               rn[c] = rE * sc;
               pn[c] = pE * sc;
               en[c] = EE[c] - sh;
-              acc_add(acc, rn[c] * rn[c], -2 * en[c]);
+              accf = fmaf(rn[c] * rn[c], pow2f(-2 * en[c] - frame), accf);
               const float rk = fabsf(rn[c]) * pow2f(kyi - en[c]);
               if (mode == 0)
                 rmax = fmaxf(rmax, rk);
@@ -1278,7 +1322,7 @@ k_mixed2d_tma(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ 
     }
     __syncthreads();
   }
-  inner_pass_tail<PASS2>(acc, rmax, st, part, nblk_part);
+  inner_pass_tail<PASS2>(Acc32{accf, frame}, rmax, st, part, nblk_part);
 }
 
 // x64 += d (kx units, unknowns only: d is zero on the sources).
@@ -1688,39 +1732,29 @@ static eik_status build_graph(MixedState *m, cudaStream_t s) {
   return EIK_OK;
 }
 
-eik_status mixed_solve(MixedState *m, const MixedArgs &a, int *inner_iters, int *outer_iters,
-                       double *res_cw, double *res_nw) {
-  static const bool trace = getenv("EIK_TRACE_MIXED") != nullptr;
+// Refinement steps restricted to the unknowns in cells with lo <= kx < hi
+// (INT_MIN / INT_MAX: all): FP64 residual, FP32 inner CG on the correction,
+// FP64 update, until the componentwise residual of the band is <= tol, the
+// step limit, or no progress.  Iterations and steps are added to *total and
+// *outer.  max_outer == 0: only the residual check.
+static eik_status refine(MixedState *m, const MixedArgs &a, int lo, int hi, int max_outer,
+                         int *total_io, int *outer_io, double *res_cw, bool trace) {
   const Grid &g = m->g;
   cudaStream_t s = a.stream;
   const int cap = m->cap;
   auto blocks = [&](int64_t n) {
     return (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, cap));
   };
-  // setup: FP32 coefficients, cell means of f, coarse distance -> exponents
-  k_sig32<<<blocks(g.n), kThreads, 0, s>>>(g.n, a.sig, m->s32);
-  k_cell_mean<<<m->cg.ncell, kThreads, 0, s>>>(g, m->cg, a.f, m->fb);
-  const size_t smem = 2 * sizeof(float) * m->cg.ncell;
-  k_coarse_exponents<<<1, 1024, smem, s>>>(g, m->cg, g.hbar / g.sqrt_c, m->fb, a.src, a.U,
-                                           a.nsrc, m->kx, m->St);
-  MCK(cudaMemsetAsync(m->x64, 0, sizeof(double) * g.n, s));
-  k_init_x64<<<(int)((a.nsrc + kThreads - 1) / kThreads), kThreads, 0, s>>>(
-      g, m->cg, m->kx, a.src, a.U, a.nsrc, m->x64);
-  m->launches[0] += 3;
-  m->launches[1] += 1;
-  MCK(cudaGetLastError());
-  eik_status gs = build_graph(m, s);
-  if (gs != EIK_OK) return gs;
-
   const double tol = a.opt.tol;
   const double red = (a.opt.inner_tol > 0) ? a.opt.inner_tol : 1e-3;
-  const int max_outer = (a.opt.max_outer > 0) ? a.opt.max_outer : 30;
-  int total = 0, outer = 0;
+  int total = *total_io, outer = 0;
   double best_cw = INFINITY;
   int stall = 0;
   eik_status result = EIK_ERR_NOT_CONVERGED;
   for (;;) {
     MixState init{};
+    init.band_lo = lo;
+    init.band_hi = hi;
     *m->h_st = init;
     MCK(cudaMemcpyAsync(m->st, m->h_st, sizeof(MixState), cudaMemcpyHostToDevice, s));
     launch_residual(m, a);
@@ -1729,7 +1763,6 @@ eik_status mixed_solve(MixedState *m, const MixedArgs &a, int *inner_iters, int 
     MCK(cudaStreamSynchronize(s));
     const double cw = m->h_st->cw;
     *res_cw = cw;
-    *res_nw = 0.0;
     if (trace)
       fprintf(stderr, "[mixed] outer %d total %d cw %.3e r_inf %.3e x_inf %.3e\n", outer, total,
               cw, m->h_st->r_inf, m->h_st->x_inf);
@@ -1737,7 +1770,15 @@ eik_status mixed_solve(MixedState *m, const MixedArgs &a, int *inner_iters, int 
       result = EIK_OK;
       break;
     }
-    if (outer >= max_outer || total >= a.opt.max_iter) break;
+    if (std::isnan(cw)) {
+      g_msg = "mixed refinement produced a non-finite residual";
+      result = EIK_ERR_BREAKDOWN;
+      break;
+    }
+    if (outer >= max_outer || total >= a.opt.max_iter) {
+      g_msg = "mixed refinement reached its step or iteration limit";
+      break;
+    }
     // (cw is infinite while some node of the iterate is not positive yet;
     // progress is then judged only once it is finite)
     if (!std::isfinite(cw) || cw < 0.5 * best_cw) {
@@ -1816,8 +1857,78 @@ eik_status mixed_solve(MixedState *m, const MixedArgs &a, int *inner_iters, int 
     m->launches[5]++;
     MCK(cudaGetLastError());
   }
+  *total_io = total;
+  *outer_io += outer;
+  return result;
+}
+
+eik_status mixed_solve(MixedState *m, const MixedArgs &a, int *inner_iters, int *outer_iters,
+                       double *res_cw, double *res_nw) {
+  static const bool trace = getenv("EIK_TRACE_MIXED") != nullptr;
+  const Grid &g = m->g;
+  cudaStream_t s = a.stream;
+  const int cap = m->cap;
+  auto blocks = [&](int64_t n) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, cap));
+  };
+  // setup: FP32 coefficients, cell means of f, coarse distance -> exponents
+  k_sig32<<<blocks(g.n), kThreads, 0, s>>>(g.n, a.sig, m->s32);
+  k_cell_mean<<<m->cg.ncell, kThreads, 0, s>>>(g, m->cg, a.f, m->fb);
+  const size_t smem = 2 * sizeof(float) * m->cg.ncell;
+  k_coarse_exponents<<<1, 1024, smem, s>>>(g, m->cg, g.hbar / g.sqrt_c, m->fb, a.src, a.U,
+                                           a.nsrc, m->kx, m->St);
+  MCK(cudaMemsetAsync(m->x64, 0, sizeof(double) * g.n, s));
+  k_init_x64<<<(int)((a.nsrc + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+      g, m->cg, m->kx, a.src, a.U, a.nsrc, m->x64);
+  m->launches[0] += 3;
+  m->launches[1] += 1;
+  MCK(cudaGetLastError());
+  eik_status gs = build_graph(m, s);
+  if (gs != EIK_OK) return gs;
+
+  const int band_bits = (a.opt.band_bits > 0) ? a.opt.band_bits : kBandBits;
+  int kmin = 0, kmax = 0;
+  if (a.opt.band_bits >= 0) {
+    std::vector<int> hk(m->cg.ncell);
+    MCK(cudaMemcpyAsync(hk.data(), m->kx, sizeof(int) * hk.size(), cudaMemcpyDeviceToHost, s));
+    MCK(cudaStreamSynchronize(s));
+    kmin = *std::min_element(hk.begin(), hk.end());
+    kmax = *std::max_element(hk.begin(), hk.end());
+  }
+  const int max_outer = (a.opt.max_outer > 0) ? a.opt.max_outer : 30;
+  int total = 0, outer = 0;
+  eik_status result;
+  if (a.opt.band_bits < 0 || kmax - kmin <= 2 * band_bits) {
+    result = refine(m, a, INT_MIN, INT_MAX, max_outer, &total, &outer, res_cw, trace);
+  } else {
+    // Level-set sweep: bands of band_bits powers of two in kx (plus an outer
+    // overlap of half a band), nearest first; everything nearer is held at
+    // its converged values, everything farther at its current ones.  Then a
+    // check of the whole grid; a further sweep where it fails.
+    const int ov = band_bits / 2;
+    result = EIK_ERR_NOT_CONVERGED;
+    for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
+      for (int lo = kmin;; lo += band_bits) {
+        const int hi = std::min(lo + band_bits + ov, kmax + 1);
+        k_sig32_band<<<blocks(g.n), kThreads, 0, s>>>(g, m->cg, m->kx, lo, hi, a.sig, m->s32);
+        m->launches[0]++;
+        MCK(cudaGetLastError());
+        if (trace) fprintf(stderr, "[mixed] sweep %d band [%d, %d)\n", sweep, lo, hi);
+        const eik_status bs = refine(m, a, lo, hi, max_outer, &total, &outer, res_cw, trace);
+        if (bs != EIK_OK && bs != EIK_ERR_NOT_CONVERGED) return bs;   // breakdown, timeout, CUDA
+        if (hi > kmax || total >= a.opt.max_iter) break;
+      }
+      k_sig32<<<blocks(g.n), kThreads, 0, s>>>(g.n, a.sig, m->s32);
+      m->launches[0]++;
+      int checks = 0;
+      result = refine(m, a, INT_MIN, INT_MAX, 0, &total, &checks, res_cw, trace);
+      if (result == EIK_OK || total >= a.opt.max_iter) break;
+    }
+    if (result == EIK_ERR_NOT_CONVERGED) g_msg = "level-set sweeps did not converge";
+  }
   *inner_iters = total;
   *outer_iters = outer;
+  *res_nw = 0.0;
   return result;
 }
 

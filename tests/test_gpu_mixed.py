@@ -26,9 +26,9 @@ def eik():
     return e
 
 
-def mixed_solve(eik, inst, tol=1e-9, boundary="half_cell", want_phi=False):
+def mixed_solve(eik, inst, tol=1e-9, boundary="half_cell", want_phi=False, band_bits=0):
     import torch
-    opt = eik.make_options(precision="mixed", tol=tol, boundary=boundary)
+    opt = eik.make_options(precision="mixed", tol=tol, boundary=boundary, band_bits=band_bits)
     f = torch.from_numpy(np.ascontiguousarray(inst.f)).cuda()
     h = eik.eik_create(inst.dims, inst.h, inst.hbar, f, inst.src_idx, inst.src_U, opt)
     S, phi, stats = eik.eik_solve(h, want_phi=want_phi)
@@ -118,3 +118,30 @@ def test_bench_tolerance_meets_S_bound(eik, precision):
     eik.eik_destroy(h)
     S_ref, _, _ = fd.solve(inst.f, inst.dims, inst.h, inst.hbar, inst.src_idx)
     assert np.max(np.abs(S.cpu().numpy().ravel() - S_ref)) <= S_ABS
+
+
+@pytest.mark.parametrize("k", [43, 132])
+def test_level_set_sweep_large_range(eik, k):
+    """Config-4 instances with hbar = 2h whose phi spans far more than 2^96
+    (S/hbar up to ~300): one global CG, FP32 or FP64 (the oracle's own CG
+    stalls on such instances), does not reach them; the mixed path sweeps
+    level-set bands of the distance estimate.  Checked against the oracle's
+    relative-form direct solve."""
+    inst = wl.config4()[k]
+    S, _, stats, _ = mixed_solve(eik, inst, tol=1e-7)
+    sys = fd.assemble(inst.f, inst.dims, inst.h, inst.hbar, inst.src_idx, inst.src_U)
+    S_ref = fd.solve_relative(sys)
+    assert np.max(S_ref) / inst.hbar > 90
+    assert np.max(np.abs(S - S_ref)) <= S_ABS
+    assert np.array_equal(S[sys.src], sys.U)
+
+
+@pytest.mark.parametrize("band_bits", [-1, 0, 24])
+def test_band_width_does_not_change_the_solution(eik, band_bits):
+    """Config 2 structure at 512^2: without sweeps, with the default bands and
+    with narrow bands, S meets the same bound against the oracle."""
+    inst = wl.config2(n=512)
+    S, _, stats, _ = mixed_solve(eik, inst, tol=1e-8, band_bits=band_bits)
+    S_ref, _, _ = fd.solve(inst.f, inst.dims, inst.h, inst.hbar, inst.src_idx)
+    assert np.max(np.abs(S - S_ref)) <= S_ABS
+    assert stats["res_cw"] <= 1e-8
