@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--c4-count", type=int, default=256,
                     help="instances in the batched workload (c4)")
     ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--inner-tol", type=float, default=0.0,
+                    help="mixed mode first inner-solve reduction (eik_options.inner_tol); "
+                         "0 library choice")
     ap.add_argument("--band-bits", type=int, default=0,
                     help="mixed mode level-set band width (eik_options.band_bits): "
                          "0 library choice, negative never sweep")
@@ -203,7 +206,7 @@ def run_ours(args):
 
     def make(prec):
         opt = eik.make_options(precision=prec, tol=args.tol, tile_override=args.tile_override,
-                               band_bits=args.band_bits)
+                               band_bits=args.band_bits, inner_tol=args.inner_tol)
         return eik.eik_create(inst.dims, inst.h, inst.hbar, f_dev, src, None, opt)
 
     modes = [args.precision] + [m for m in ("fp64", "mixed") if m != args.precision]
@@ -292,7 +295,8 @@ def run_batch(args):
     insts = wl.config4(count=args.c4_count)
     n_unk = [i.n - len(np.unique(i.src_idx)) for i in insts]
     opt = eik.make_options(precision=args.precision, tol=args.tol,
-                           tile_override=args.tile_override, band_bits=args.band_bits)
+                           tile_override=args.tile_override, band_bits=args.band_bits,
+                           inner_tol=args.inner_tol)
     b = eik.eik_create_batch(insts, opt)
     S = torch.empty(b.n, dtype=torch.float64, device="cuda")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")

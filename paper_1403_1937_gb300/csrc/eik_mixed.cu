@@ -46,7 +46,9 @@ constexpr int kInnerGraphIters = 32;   // even: the buffer sets alternate
 constexpr int kNoExp = 30000;          // exponent of an all-zero node
 constexpr int kMaxCells = 16384;
 constexpr int kBandBits = 48;          // level-set band width (powers of two of phi)
-constexpr int kMaxSweeps = 3;
+constexpr int kMaxSweeps = 4;
+constexpr int kMinOverlapBits = 32;    // band overlap (powers of two), at least
+constexpr int kGlobalFinishBits = 160; // ranges that a global refinement still handles
 
 thread_local std::string g_msg = "no error";   // per host thread (batches)
 
@@ -1033,7 +1035,7 @@ k_mixed2d(Grid g, CellGrid cg, int tiles_x, int ntiles, const int *__restrict__ 
 // grid arrive as zeros (TMA fill); a neighbour with u = 0 is left out of the
 // exponent minimum, so the zero fill needs no special case.
 constexpr int kTmaTX = 128;                 // tile columns
-constexpr int kTmaStages = 2;
+constexpr int kTmaStages = 2;               // default stage count (2D)
 constexpr unsigned long long kTmaWaitNs = 200ull * 1000 * 1000;   // 0.2 s
 
 template <int TY>
@@ -1049,7 +1051,9 @@ struct TmaTile {
   static constexpr int OFF_D = OFF_E + E_BYTES, OFF_X = OFF_D + C_BYTES;
   static constexpr int STAGE1 = OFF_D;                     // pass 1 stage bytes
   static constexpr int STAGE2 = OFF_X + C_BYTES;           // pass 2 stage bytes
-  static constexpr int smem(bool pass2) { return kTmaStages * (pass2 ? STAGE2 : STAGE1) + 128; }
+  static constexpr int smem(bool pass2, int ns = kTmaStages) {
+    return ns * (pass2 ? STAGE2 : STAGE1) + 128;
+  }
 };
 
 struct TmaMaps {
@@ -1149,7 +1153,7 @@ __device__ __forceinline__ void tcol_load(const unsigned char *stage, int j, int
   n = (u != 0.f) ? (int)se[j * T::EW + c + 8] : kNoExp;
 }
 
-template <bool PASS2, int TY, int RG>
+template <bool PASS2, int TY, int RG, int NS>
 __global__ void __launch_bounds__(64 * RG, 1)
 k_mixed2d_tma(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtensorMap tm_p,
               const __grid_constant__ CUtensorMap tm_e, const __grid_constant__ CUtensorMap tm_s,
@@ -1161,7 +1165,7 @@ k_mixed2d_tma(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ 
   constexpr int RW = TY / RG;   // rows marched by one warp
   static_assert(TY % RG == 0, "rows per warp");
   extern __shared__ unsigned char tma_smem_raw[];
-  __shared__ __align__(8) uint64_t bar[kTmaStages];
+  __shared__ __align__(8) uint64_t bar[NS];
   if (st->done) return;
   unsigned char *smem = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(tma_smem_raw) + 127) & ~uintptr_t(127));
@@ -1190,14 +1194,14 @@ k_mixed2d_tma(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ 
   };
 
   if (tid == 0) {
-    for (int k = 0; k < kTmaStages; ++k) mbar_init(&bar[k], 1);
+    for (int k = 0; k < NS; ++k) mbar_init(&bar[k], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   __syncthreads();
   const int first = blockIdx.x, step = gridDim.x;
   if (tid == 0)
-    for (int k = 0; k < kTmaStages; ++k)
+    for (int k = 0; k < NS; ++k)
       if (first + k * step < ntiles) issue(first + k * step, k);
 
   // Inner-product terms are summed in FP32 relative to 2^frame, the scale of
@@ -1209,8 +1213,8 @@ k_mixed2d_tma(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ 
   bool fault = false;
   int k = 0;
   for (int t = first; t < ntiles; t += step, ++k) {
-    const int stg = k % kTmaStages;
-    const uint32_t parity = (uint32_t)(k / kTmaStages) & 1u;
+    const int stg = k % NS;
+    const uint32_t parity = (uint32_t)(k / NS) & 1u;
     const bool ok = mbar_wait_bounded(&bar[stg], parity);
     if (__syncthreads_or(!ok)) {
       fault = true;
@@ -1305,20 +1309,283 @@ k_mixed2d_tma(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ 
       C = B;
     }
     __syncthreads();   // every thread is done with this stage
-    if (tid == 0 && t + kTmaStages * step < ntiles) {
+    if (tid == 0 && t + NS * step < ntiles) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(t + kTmaStages * step, stg);
+      issue(t + NS * step, stg);
     }
   }
   if (fault) {
     // leave no copy in flight: wait (bounded) for every stage still pending
     if (tid == 0) {
       atomicExch(&st->fault, 1);
-      for (int kk = k; kk < k + kTmaStages; ++kk) {
+      for (int kk = k; kk < k + NS; ++kk) {
         const int t = first + kk * step;
         if (t >= ntiles) break;
-        mbar_wait_bounded(&bar[kk % kTmaStages], (uint32_t)(kk / kTmaStages) & 1u);
+        mbar_wait_bounded(&bar[kk % NS], (uint32_t)(kk / NS) & 1u);
       }
+    }
+    __syncthreads();
+  }
+  inner_pass_tail<PASS2>(Acc32{accf, frame}, rmax, st, part, nblk_part);
+}
+
+// ------------------------------------ 3D inner CG, TMA-staged z-marching
+// A tile is 128 columns x TY rows x zc planes.  The block streams the tile's
+// zc + 2 planes (with their x/y halo, box 136 x (TY + 2) x 1, and the
+// int16 exponents with 144 x (TY + 2)) through a ring of kTma3Stages
+// shared-memory stages, each guarded by an mbarrier with a bounded wait.
+// One warp owns one row y of 64 columns (2 per lane) and marches in z: the
+// rows at z - 1 and z (u, exponents) stay in registers, the row at z + 1 and
+// the y neighbours at z come from shared memory, the x neighbours by warp
+// shuffle.  Plane q of the block's stream goes to stage q % kTma3Stages;
+// after the block is done with a plane, the plane kTma3Stages further on is
+// issued into its stage.  Arithmetic per node as in k_mixed2d_tma.
+constexpr int kTma3Stages = 4;
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
+                                            uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// u and neighbour exponents of the lane's two columns in smem row j.
+template <int TY>
+__device__ __forceinline__ void urow_load(const unsigned char *stage, int j, int lc, float beta,
+                                          float &u0, float &u1, int &n0, int &n1) {
+  using T = TmaTile<TY>;
+  const float *sr = reinterpret_cast<const float *>(stage + T::OFF_R);
+  const float *sp = reinterpret_cast<const float *>(stage + T::OFF_P);
+  const float *ss = reinterpret_cast<const float *>(stage + T::OFF_S);
+  const short *se = reinterpret_cast<const short *>(stage + T::OFF_E);
+  const int fo = j * T::FW + lc + 4;
+  const float2 r = *reinterpret_cast<const float2 *>(sr + fo);
+  const float2 p = *reinterpret_cast<const float2 *>(sp + fo);
+  const float2 sg = *reinterpret_cast<const float2 *>(ss + fo);
+  const unsigned int ee = *reinterpret_cast<const unsigned int *>(se + j * T::EW + lc + 8);
+  u0 = sg.x * fmaf(beta, p.x, r.x);
+  u1 = sg.y * fmaf(beta, p.y, r.y);
+  n0 = (u0 != 0.f) ? (int)(short)(ee & 0xffffu) : kNoExp;
+  n1 = (u1 != 0.f) ? (int)(short)(ee >> 16) : kNoExp;
+}
+
+__device__ __forceinline__ float q_node3_le0(float pt, float sg, int ei, float uL, int eL,
+                                             float uR, int eR, float uS, int eS, float uN, int eN,
+                                             float uD, int eD, float uU, int eU, float wx,
+                                             float wy, float wz, int &E) {
+  const int m = min(min(ei, min(eL, eR)), min(min(eS, eN), min(eD, eU)));
+  E = m;
+  const float a1 = uL * pow2f_le0(m - eL) + uR * pow2f_le0(m - eR);
+  const float a2 = uS * pow2f_le0(m - eS) + uN * pow2f_le0(m - eN);
+  const float a3 = uD * pow2f_le0(m - eD) + uU * pow2f_le0(m - eU);
+  return fmaf(-sg, fmaf(wx, a1, fmaf(wy, a2, wz * a3)), pt * pow2f_le0(m - ei));
+}
+
+template <bool PASS2, int TY>
+__global__ void __launch_bounds__(64 * TY, 1)
+k_mixed3d_tma(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtensorMap tm_p,
+              const __grid_constant__ CUtensorMap tm_e, const __grid_constant__ CUtensorMap tm_s,
+              const __grid_constant__ CUtensorMap tm_d, const __grid_constant__ CUtensorMap tm_x,
+              Grid g, CellGrid cg, int tiles_x, int tiles_y, int zc, int ntiles,
+              const int *__restrict__ kx, float *__restrict__ r32o, float *__restrict__ p32o,
+              short *__restrict__ e16o, float *__restrict__ d32, MixState *st, double *part,
+              int nblk_part) {
+  using T = TmaTile<TY>;
+  constexpr int NS = kTma3Stages;
+  extern __shared__ unsigned char tma_smem_raw[];
+  __shared__ __align__(8) uint64_t bar[NS];
+  if (st->done) return;
+  unsigned char *smem = reinterpret_cast<unsigned char *>(
+      (reinterpret_cast<uintptr_t>(tma_smem_raw) + 127) & ~uintptr_t(127));
+  constexpr int STAGE = PASS2 ? T::STAGE2 : T::STAGE1;
+  const float beta = (float)st->beta, alpha = (float)st->alpha;
+  const int mode = st->mode;
+  const float theta = st->theta;
+  const bool want_x = PASS2 && mode != 0;
+  const uint32_t tx_bytes =
+      3 * (T::FW * T::H * 4) + T::EW * T::H * 2 + (PASS2 ? T::C_BYTES : 0) +
+      (want_x ? T::C_BYTES : 0);
+  const int frame = st->rho_s;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int cw = warp & 1, ry = warp >> 1;
+  const bool half = g.boundary == EIK_BOUNDARY_HALF_CELL;
+  const int PL = zc + 2;   // planes per tile
+  const int my_tiles =
+      (blockIdx.x < ntiles) ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+  const int nq = my_tiles * PL;
+  int nissued = 0;   // planes issued so far (thread 0)
+
+  auto issue = [&](int q) {
+    nissued = q + 1;
+    const int k = q / PL, j = q % PL;
+    const int t = blockIdx.x + k * gridDim.x;
+    const int stg = q % NS;
+    const int xt = t % tiles_x, rest = t / tiles_x;
+    const int x0 = xt * kTmaTX, y0 = (rest % tiles_y) * TY, zp = (rest / tiles_y) * zc - 1 + j;
+    unsigned char *dst = smem + stg * STAGE;
+    mbar_expect_tx(&bar[stg], tx_bytes);
+    tma_load_3d(dst + T::OFF_R, &tm_r, x0 - 4, y0 - 1, zp, &bar[stg]);
+    tma_load_3d(dst + T::OFF_P, &tm_p, x0 - 4, y0 - 1, zp, &bar[stg]);
+    tma_load_3d(dst + T::OFF_S, &tm_s, x0 - 4, y0 - 1, zp, &bar[stg]);
+    tma_load_3d(dst + T::OFF_E, &tm_e, x0 - 8, y0 - 1, zp, &bar[stg]);
+    if (PASS2) tma_load_3d(dst + T::OFF_D, &tm_d, x0, y0, zp, &bar[stg]);
+    if (want_x) tma_load_3d(dst + T::OFF_X, &tm_x, x0, y0, zp, &bar[stg]);
+  };
+  auto wait = [&](int q) {
+    return mbar_wait_bounded(&bar[q % NS], (uint32_t)(q / NS) & 1u);
+  };
+  auto stage = [&](int q) -> const unsigned char * { return smem + (q % NS) * STAGE; };
+  // the block is done with plane q: issue plane q + NS into its stage
+  auto release = [&](int q) {
+    __syncthreads();
+    if (tid == 0 && q + NS < nq) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(q + NS);
+    }
+  };
+
+  if (tid == 0) {
+    for (int k = 0; k < NS; ++k) mbar_init(&bar[k], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int q = 0; q < NS && q < nq; ++q) issue(q);
+
+  float accf = 0.f, rmax = 0.f;
+  bool fault = false;
+  int qwait = 0;   // first plane not yet waited for
+  const int lc = 64 * cw + 2 * lane;
+  const int hc = (lane == 0) ? lc - 1 : lc + 2;
+  for (int k = 0; k < my_tiles && !fault; ++k) {
+    const int t = blockIdx.x + k * gridDim.x;
+    const int xt = t % tiles_x, rest = t / tiles_x;
+    const int x = xt * kTmaTX + lc, y = (rest % tiles_y) * TY + ry;
+    const int z0 = (rest / tiles_y) * zc;
+    const int q0 = k * PL;
+    const float wyz = (half && (y == 0 || y == g.ny - 1)) ? 0.5f : 1.f;   // hy
+    const float hx0 = (half && x == 0) ? 0.5f : 1.f;
+    const float hx1 = (half && x + 1 == g.nx - 1) ? 0.5f : 1.f;
+    // prologue: rows at z0 - 1 (u, exponents) and z0 (full)
+    bool ok = wait(q0);
+    ok = wait(q0 + 1) && ok;
+    qwait = q0 + 2;
+    if (__syncthreads_or(!ok)) {
+      fault = true;
+      qwait = q0;
+      break;
+    }
+    float uA0, uA1;
+    int nA0, nA1;
+    urow_load<TY>(stage(q0), ry + 1, lc, beta, uA0, uA1, nA0, nA1);
+    TRow C, B;
+    trow_load<TY>(stage(q0 + 1), ry + 1, lc, beta, C);
+    release(q0);
+    for (int i = 0; i < zc; ++i) {
+      const int qb = q0 + i + 2;
+      const bool okb = wait(qb);
+      qwait = qb + 1;
+      if (__syncthreads_or(!okb)) {
+        fault = true;
+        qwait = qb;
+        break;
+      }
+      const unsigned char *Sc = stage(qb - 1);
+      trow_load<TY>(stage(qb), ry + 1, lc, beta, B);
+      float uS0, uS1, uN0, uN1;
+      int nS0, nS1, nN0, nN1;
+      urow_load<TY>(Sc, ry, lc, beta, uS0, uS1, nS0, nS1);       // y - 1
+      urow_load<TY>(Sc, ry + 2, lc, beta, uN0, uN1, nN0, nN1);   // y + 1
+      float uh = 0.f;
+      int nh = kNoExp;
+      if (lane == 0 || lane == 31) tcol_load<TY>(Sc, ry + 1, hc, beta, uh, nh);
+      float uL = __shfl_up_sync(0xffffffffu, C.u1, 1);
+      int nL = __shfl_up_sync(0xffffffffu, C.n1, 1);
+      float uR = __shfl_down_sync(0xffffffffu, C.u0, 1);
+      int nR = __shfl_down_sync(0xffffffffu, C.n0, 1);
+      if (lane == 0) {
+        uL = uh;
+        nL = nh;
+      }
+      if (lane == 31) {
+        uR = uh;
+        nR = nh;
+      }
+      const int z = z0 + i;
+      if (x < g.nx && y < g.ny && z < g.nz) {
+        const float hz = (half && (z == 0 || z == g.nz - 1)) ? 0.5f : 1.f;
+        // x edges carry hy hz, y edges hx hz, z edges hx hy
+        int E0, E1;
+        const float q0v = q_node3_le0(C.pt0, C.s0, C.e0, uL, nL, C.u1, C.n1, uS0, nS0, uN0, nN0,
+                                      uA0, nA0, B.u0, B.n0, wyz * hz, hx0 * hz, hx0 * wyz, E0);
+        const float q1v = q_node3_le0(C.pt1, C.s1, C.e1, C.u0, C.n0, uR, nR, uS1, nS1, uN1, nN1,
+                                      uA1, nA1, B.u1, B.n1, wyz * hz, hx1 * hz, hx1 * wyz, E1);
+        if (!PASS2) {
+          accf = fmaf(C.pt0 * q0v, pow2f(-(C.e0 + E0) - frame), accf);
+          accf = fmaf(C.pt1 * q1v, pow2f(-(C.e1 + E1) - frame), accf);
+        } else {
+          const int li = ry * kTmaTX + lc;   // tile-local index, no halo
+          const float2 dd = *reinterpret_cast<const float2 *>(Sc + T::OFF_D + 4 * li);
+          float2 xr = make_float2(0.f, 0.f);
+          if (want_x) xr = *reinterpret_cast<const float2 *>(Sc + T::OFF_X + 4 * li);
+          const int kyi = kx[cell_of(cg, x, y, z)];   // x, x+1: one cell
+          float d[2] = {dd.x, dd.y}, rn[2], pn[2];
+          int en[2];
+          const float pt[2] = {C.pt0, C.pt1}, rr[2] = {C.r0, C.r1}, qq[2] = {q0v, q1v};
+          const int ee[2] = {C.e0, C.e1}, EE[2] = {E0, E1};
+          const float xx[2] = {xr.x, xr.y};
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            if (pt[c] != 0.f) d[c] = fmaf(alpha * pt[c], pow2f(kyi - ee[c]), d[c]);
+            const float f = pow2f_le0(EE[c] - ee[c]);
+            const float rE = fmaf(-alpha, qq[c], rr[c] * f);
+            const float pE = pt[c] * f;
+            const float mx = fmaxf(fabsf(rE), fabsf(pE));
+            if (mx > 0.f && mx <= 3.4e38f) {
+              const int sh = expof(mx);
+              const float sc = __int_as_float((127 - sh) << 23);
+              rn[c] = rE * sc;
+              pn[c] = pE * sc;
+              en[c] = EE[c] - sh;
+              accf = fmaf(rn[c] * rn[c], pow2f(-2 * en[c] - frame), accf);
+              const float rk = fabsf(rn[c]) * pow2f(kyi - en[c]);
+              if (mode == 0)
+                rmax = fmaxf(rmax, rk);
+              else if (rk > theta * fabsf(xx[c] + d[c]))
+                rmax = 1.f;
+            } else {
+              rn[c] = 0.f;
+              pn[c] = 0.f;
+              en[c] = kNoExp;
+              if (!(mx <= 3.4e38f)) rmax = INFINITY;
+            }
+          }
+          const int64_t o = ((int64_t)z * g.ny + y) * g.nx + x;
+          *reinterpret_cast<float2 *>(d32 + o) = make_float2(d[0], d[1]);
+          *reinterpret_cast<float2 *>(r32o + o) = make_float2(rn[0], rn[1]);
+          *reinterpret_cast<float2 *>(p32o + o) = make_float2(pn[0], pn[1]);
+          *reinterpret_cast<unsigned int *>(e16o + o) = pack2(en[0], en[1]);
+        }
+      }
+      uA0 = C.u0;
+      uA1 = C.u1;
+      nA0 = C.n0;
+      nA1 = C.n1;
+      C = B;
+      release(qb - 1);
+    }
+    if (!fault) release(q0 + zc + 1);
+  }
+  if (fault) {
+    // leave no copy in flight: wait (bounded) for every plane issued and not
+    // yet waited for
+    if (tid == 0) {
+      atomicExch(&st->fault, 1);
+      for (int q = qwait; q < nissued; ++q)
+        mbar_wait_bounded(&bar[q % NS], (uint32_t)(q / NS) & 1u);
     }
     __syncthreads();
   }
@@ -1380,6 +1647,7 @@ struct MixedState {
   int tiles_x = 0, ntiles2d = 0, nblk2d = 0;
   int tma = 0;                   // TMA-staged 2D kernels: variant index (0 = off)
   int tma_tiles_x = 0, tma_ntiles = 0, tma_nblk1 = 0, tma_nblk2 = 0;
+  int tma_tiles_y = 0, tma_zc = 0;   // 3D: rows per tile come from the variant
   CUtensorMap tm_r[2], tm_p[2], tm_e[2], tm_s, tm_d, tm_x;
   float *s32 = nullptr, *fb = nullptr, *St = nullptr, *d32 = nullptr, *xref = nullptr;
   float *r32[2] = {nullptr, nullptr}, *p32[2] = {nullptr, nullptr};
@@ -1441,22 +1709,24 @@ const char *mixed_last_error() { return g_msg.c_str(); }
 // TMA variants: (rows per tile, row groups per block); 2 warps per row
 // group.  Variant 3 (16 rows, 8 warps) is the library default: it measured
 // fastest on the 2048^2 workload.
-constexpr int kTmaVariantCount = 4;
-constexpr int kTmaTYs[kTmaVariantCount] = {16, 32, 16, 32};   // row groups: 2, 4, 4, 2
+constexpr int kTmaVariantCount = 9;
+// rows per tile.  2D (row groups, stages): 1 (2, 2), 2 (4, 2), 3 (4, 2),
+// 4 (2, 2), 7 (4, 4), 8 (4, 3), 9 (2, 4); variants 5, 6 are the 3D kernels.
+constexpr int kTmaTYs[kTmaVariantCount] = {16, 32, 16, 32, 4, 8, 8, 16, 8};
 
-template <int TY, int RG>
+template <int TY, int RG, int NS>
 static bool tma_setup_t(MixedState *m, int num_sms) {
   using T = TmaTile<TY>;
-  const int s1 = T::smem(false), s2 = T::smem(true);
-  if (cudaFuncSetAttribute(k_mixed2d_tma<false, TY, RG>,
+  const int s1 = T::smem(false, NS), s2 = T::smem(true, NS);
+  if (cudaFuncSetAttribute(k_mixed2d_tma<false, TY, RG, NS>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, s1) != cudaSuccess ||
-      cudaFuncSetAttribute(k_mixed2d_tma<true, TY, RG>,
+      cudaFuncSetAttribute(k_mixed2d_tma<true, TY, RG, NS>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, s2) != cudaSuccess)
     return false;
   int per1 = 0, per2 = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, k_mixed2d_tma<false, TY, RG>, 64 * RG,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, k_mixed2d_tma<false, TY, RG, NS>, 64 * RG,
                                                     s1) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_mixed2d_tma<true, TY, RG>, 64 * RG,
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_mixed2d_tma<true, TY, RG, NS>, 64 * RG,
                                                     s2) != cudaSuccess)
     return false;
   if (per1 < 1 || per2 < 1) return false;
@@ -1467,13 +1737,61 @@ static bool tma_setup_t(MixedState *m, int num_sms) {
   return true;
 }
 
+// 3D variants 5 / 6: TY = 4 / 8 rows per tile (2 warps per row).  The
+// number of planes per tile, zc, is chosen to balance the tiles over the
+// resident blocks.
+template <int TY>
+static bool tma3_setup_t(MixedState *m, int num_sms) {
+  using T = TmaTile<TY>;
+  const int s1 = kTma3Stages * T::STAGE1 + 128, s2 = kTma3Stages * T::STAGE2 + 128;
+  if (cudaFuncSetAttribute(k_mixed3d_tma<false, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           s1) != cudaSuccess ||
+      cudaFuncSetAttribute(k_mixed3d_tma<true, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           s2) != cudaSuccess)
+    return false;
+  int per1 = 0, per2 = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, k_mixed3d_tma<false, TY>, 64 * TY,
+                                                    s1) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_mixed3d_tma<true, TY>, 64 * TY,
+                                                    s2) != cudaSuccess)
+    return false;
+  if (per1 < 1 || per2 < 1) return false;
+  const Grid &g = m->g;
+  m->tma_tiles_x = (g.nx + kTmaTX - 1) / kTmaTX;
+  m->tma_tiles_y = (g.ny + TY - 1) / TY;
+  const int64_t plane_tiles = (int64_t)m->tma_tiles_x * m->tma_tiles_y;
+  int best_zc = 8;
+  int64_t best_cost = INT64_MAX;
+  for (int zc : {8, 16, 32, 64}) {
+    const int64_t nt = plane_tiles * ((g.nz + zc - 1) / zc);
+    const int64_t nb = std::min<int64_t>(nt, (int64_t)per2 * num_sms);
+    const int64_t cost = ((nt + nb - 1) / nb) * (zc + 2);
+    if (cost <= best_cost) {
+      best_cost = cost;
+      best_zc = zc;
+    }
+  }
+  const int64_t nt = plane_tiles * ((g.nz + best_zc - 1) / best_zc);
+  if (nt > INT_MAX / (best_zc + 2)) return false;
+  m->tma_zc = best_zc;
+  m->tma_ntiles = (int)nt;
+  m->tma_nblk1 = (int)std::min<int64_t>(nt, (int64_t)per1 * num_sms);
+  m->tma_nblk2 = (int)std::min<int64_t>(nt, (int64_t)per2 * num_sms);
+  return true;
+}
+
 static bool tma_setup(MixedState *m, int v, int num_sms) {
   m->tma = v;
   switch (v) {
-    case 1: return tma_setup_t<16, 2>(m, num_sms);
-    case 2: return tma_setup_t<32, 4>(m, num_sms);
-    case 3: return tma_setup_t<16, 4>(m, num_sms);
-    case 4: return tma_setup_t<32, 2>(m, num_sms);
+    case 1: return tma_setup_t<16, 2, 2>(m, num_sms);
+    case 2: return tma_setup_t<32, 4, 2>(m, num_sms);
+    case 3: return tma_setup_t<16, 4, 2>(m, num_sms);
+    case 4: return tma_setup_t<32, 2, 2>(m, num_sms);
+    case 5: return tma3_setup_t<4>(m, num_sms);
+    case 6: return tma3_setup_t<8>(m, num_sms);
+    case 7: return tma_setup_t<8, 4, 4>(m, num_sms);
+    case 8: return tma_setup_t<16, 4, 3>(m, num_sms);
+    case 9: return tma_setup_t<8, 2, 4>(m, num_sms);
   }
   return false;
 }
@@ -1496,35 +1814,37 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 2D tiled tensor map over an nx x ny row-major array; box bw x bh elements.
-static bool encode_2d(CUtensorMap *map, void *base, bool is_short, int nx, int ny, int bw,
-                      int bh) {
+// Tiled tensor map over a row-major nx x ny (x nz) array, box bw x bh (x 1)
+// elements; nz == 0 gives a 2D map.
+static bool encode_map(CUtensorMap *map, void *base, bool is_short, int nx, int ny, int nz,
+                       int bw, int bh) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   const size_t es = is_short ? 2 : 4;
-  const cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
-  const cuuint64_t strides[1] = {(cuuint64_t)nx * es};
-  const cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
-  const cuuint32_t estr[2] = {1, 1};
-  return fn(map, is_short ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
-            base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+  const cuuint32_t rank = nz > 0 ? 3 : 2;
+  const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)(nz > 0 ? nz : 1)};
+  const cuuint64_t strides[2] = {(cuuint64_t)nx * es, (cuuint64_t)nx * ny * es};
+  const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(map, is_short ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+            rank, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 static bool tma_encode(MixedState *m) {
   const int ty = kTmaTYs[m->tma - 1];
-  const int nx = m->g.nx, ny = m->g.ny;
+  const int nx = m->g.nx, ny = m->g.ny, nz = (m->g.ndim == 3) ? m->g.nz : 0;
   const int fw = kTmaTX + 8, ew = kTmaTX + 16, h = ty + 2;
   bool ok = true;
   for (int k = 0; k < 2; ++k) {
-    ok = ok && encode_2d(&m->tm_r[k], m->r32[k], false, nx, ny, fw, h);
-    ok = ok && encode_2d(&m->tm_p[k], m->p32[k], false, nx, ny, fw, h);
-    ok = ok && encode_2d(&m->tm_e[k], m->e16[k], true, nx, ny, ew, h);
+    ok = ok && encode_map(&m->tm_r[k], m->r32[k], false, nx, ny, nz, fw, h);
+    ok = ok && encode_map(&m->tm_p[k], m->p32[k], false, nx, ny, nz, fw, h);
+    ok = ok && encode_map(&m->tm_e[k], m->e16[k], true, nx, ny, nz, ew, h);
   }
-  ok = ok && encode_2d(&m->tm_s, m->s32, false, nx, ny, fw, h);
-  ok = ok && encode_2d(&m->tm_d, m->d32, false, nx, ny, kTmaTX, ty);
-  ok = ok && encode_2d(&m->tm_x, m->xref, false, nx, ny, kTmaTX, ty);
+  ok = ok && encode_map(&m->tm_s, m->s32, false, nx, ny, nz, fw, h);
+  ok = ok && encode_map(&m->tm_d, m->d32, false, nx, ny, nz, kTmaTX, ty);
+  ok = ok && encode_map(&m->tm_x, m->xref, false, nx, ny, nz, kTmaTX, ty);
   return ok;
 }
 
@@ -1566,7 +1886,10 @@ eik_status mixed_create(MixedState **out, const Grid &g, const TileCount &tc, in
   // rows with 4 / 2 columns per lane, 4..7 TMA-staged tiles (variants 1..4
   // listed at kTmaTYs)
   const int vec = (tile_override == 2) ? 4 : 2;
-  const bool tma_ok = g.ndim == 2 && g.nx % 8 == 0 && (tile_override == 0 || tile_override >= 4);
+  const bool tma_ok = g.ndim == 2 && g.nx % 8 == 0 &&
+                      (tile_override == 0 || (tile_override >= 4 && tile_override <= 7) ||
+                       (tile_override >= 10 && tile_override <= 12));
+  const bool tma3_ok = g.ndim == 3 && g.nx % 8 == 0 && (tile_override == 0 || tile_override == 8 || tile_override == 9);
   const bool march_ok = g.ndim == 2 && g.nx % vec == 0 &&
                         (tile_override == 0 || tile_override == 2 || tile_override == 3);
   if (march_ok) {
@@ -1583,10 +1906,18 @@ eik_status mixed_create(MixedState **out, const Grid &g, const TileCount &tc, in
     m->nblk2d = std::min(m->ntiles2d, per * num_sms);
   }
   if (tma_ok) {
+    // tile_override 4..7 -> variants 1..4, 10..12 -> variants 7..9
     const int v = (tile_override >= 4) ? tile_override - 3 : 3;   // default: 16 rows, 8 warps
     if (v <= kTmaVariantCount && tma_setup(m, v, num_sms)) {
       m->rows2d = false;
     } else {
+      m->tma = 0;
+      cudaGetLastError();
+    }
+  }
+  if (tma3_ok) {
+    const int v = (tile_override == 9) ? 6 : 5;   // default: 4 rows per tile
+    if (!tma_setup(m, v, num_sms)) {
       m->tma = 0;
       cudaGetLastError();
     }
@@ -1656,27 +1987,50 @@ static void launch_iteration(MixedState *m, int set, cudaStream_t s, bool timed 
   double *p1 = m->part;
   double *p2 = m->part + 3 * (size_t)m->nblk_part;
   if (m->tma) {
-#define EIK_LAUNCH_TMA(TY, RG)                                                                  \
+#define EIK_LAUNCH_TMA(TY, RG, NS)                                                              \
   do {                                                                                          \
     if (timed) cudaEventRecord(m->ev[0], s);                                                    \
-    k_mixed2d_tma<false, TY, RG><<<m->tma_nblk1, 64 * RG, TmaTile<TY>::smem(false), s>>>(       \
+    k_mixed2d_tma<false, TY, RG, NS>                                                            \
+        <<<m->tma_nblk1, 64 * RG, TmaTile<TY>::smem(false, NS), s>>>(                           \
         m->tm_r[a], m->tm_p[a], m->tm_e[a], m->tm_s, m->tm_d, m->tm_x, m->g, m->cg,             \
         m->tma_tiles_x, m->tma_ntiles, m->kx, nullptr, nullptr, nullptr, m->d32, m->st, p1,     \
         m->nblk_part);                                                                          \
     if (timed) cudaEventRecord(m->ev[1], s);                                                    \
-    k_mixed2d_tma<true, TY, RG><<<m->tma_nblk2, 64 * RG, TmaTile<TY>::smem(true), s>>>(         \
+    k_mixed2d_tma<true, TY, RG, NS>                                                             \
+        <<<m->tma_nblk2, 64 * RG, TmaTile<TY>::smem(true, NS), s>>>(                            \
         m->tm_r[a], m->tm_p[a], m->tm_e[a], m->tm_s, m->tm_d, m->tm_x, m->g, m->cg,             \
         m->tma_tiles_x, m->tma_ntiles, m->kx, m->r32[b], m->p32[b], m->e16[b], m->d32, m->st,   \
         p2, m->nblk_part);                                                                      \
     if (timed) cudaEventRecord(m->ev[2], s);                                                    \
   } while (0)
+#define EIK_LAUNCH_TMA3(TY)                                                                     \
+  do {                                                                                          \
+    using T3 = TmaTile<TY>;                                                                     \
+    if (timed) cudaEventRecord(m->ev[0], s);                                                    \
+    k_mixed3d_tma<false, TY><<<m->tma_nblk1, 64 * TY, kTma3Stages * T3::STAGE1 + 128, s>>>(     \
+        m->tm_r[a], m->tm_p[a], m->tm_e[a], m->tm_s, m->tm_d, m->tm_x, m->g, m->cg,             \
+        m->tma_tiles_x, m->tma_tiles_y, m->tma_zc, m->tma_ntiles, m->kx, nullptr, nullptr,      \
+        nullptr, m->d32, m->st, p1, m->nblk_part);                                              \
+    if (timed) cudaEventRecord(m->ev[1], s);                                                    \
+    k_mixed3d_tma<true, TY><<<m->tma_nblk2, 64 * TY, kTma3Stages * T3::STAGE2 + 128, s>>>(      \
+        m->tm_r[a], m->tm_p[a], m->tm_e[a], m->tm_s, m->tm_d, m->tm_x, m->g, m->cg,             \
+        m->tma_tiles_x, m->tma_tiles_y, m->tma_zc, m->tma_ntiles, m->kx, m->r32[b], m->p32[b],  \
+        m->e16[b], m->d32, m->st, p2, m->nblk_part);                                            \
+    if (timed) cudaEventRecord(m->ev[2], s);                                                    \
+  } while (0)
     switch (m->tma) {
-      case 1: EIK_LAUNCH_TMA(16, 2); break;
-      case 2: EIK_LAUNCH_TMA(32, 4); break;
-      case 3: EIK_LAUNCH_TMA(16, 4); break;
-      default: EIK_LAUNCH_TMA(32, 2); break;
+      case 1: EIK_LAUNCH_TMA(16, 2, 2); break;
+      case 2: EIK_LAUNCH_TMA(32, 4, 2); break;
+      case 3: EIK_LAUNCH_TMA(16, 4, 2); break;
+      case 4: EIK_LAUNCH_TMA(32, 2, 2); break;
+      case 5: EIK_LAUNCH_TMA3(4); break;
+      case 6: EIK_LAUNCH_TMA3(8); break;
+      case 7: EIK_LAUNCH_TMA(8, 4, 4); break;
+      case 8: EIK_LAUNCH_TMA(16, 4, 3); break;
+      default: EIK_LAUNCH_TMA(8, 2, 4); break;
     }
 #undef EIK_LAUNCH_TMA
+#undef EIK_LAUNCH_TMA3
     return;
   }
   if (m->rows2d) {
@@ -1902,10 +2256,13 @@ eik_status mixed_solve(MixedState *m, const MixedArgs &a, int *inner_iters, int 
     result = refine(m, a, INT_MIN, INT_MAX, max_outer, &total, &outer, res_cw, trace);
   } else {
     // Level-set sweep: bands of band_bits powers of two in kx (plus an outer
-    // overlap of half a band), nearest first; everything nearer is held at
-    // its converged values, everything farther at its current ones.  Then a
-    // check of the whole grid; a further sweep where it fails.
-    const int ov = band_bits / 2;
+    // overlap), nearest first; everything nearer is held at its converged
+    // values, everything farther at its current ones.  Then a check of the
+    // whole grid; a further sweep where it fails.  The overlap is at least
+    // kMinOverlapBits: kx comes from a coarse estimate whose error measured
+    // up to ~20 powers of two, and the influence of the band's outer data
+    // falls off like 2^(-2 x true overlap).
+    const int ov = std::max(band_bits / 2, kMinOverlapBits);
     result = EIK_ERR_NOT_CONVERGED;
     for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
       for (int lo = kmin;; lo += band_bits) {
@@ -1923,6 +2280,11 @@ eik_status mixed_solve(MixedState *m, const MixedArgs &a, int *inner_iters, int 
       int checks = 0;
       result = refine(m, a, INT_MIN, INT_MAX, 0, &total, &checks, res_cw, trace);
       if (result == EIK_OK || total >= a.opt.max_iter) break;
+    }
+    if (result == EIK_ERR_NOT_CONVERGED && kmax - kmin <= kGlobalFinishBits &&
+        total < a.opt.max_iter) {
+      // a moderate range: finish with refinement steps over the whole grid
+      result = refine(m, a, INT_MIN, INT_MAX, max_outer, &total, &outer, res_cw, trace);
     }
     if (result == EIK_ERR_NOT_CONVERGED) g_msg = "level-set sweeps did not converge";
   }
