@@ -108,8 +108,8 @@ typedef struct {
                          A variant whose condition fails falls back to the
                          generic kernels. */
   double inner_tol;   /* mixed mode: factor by which the first FP32 inner
-                         solve reduces the residual (scaled max norm);
-                         0 = library choice (1e-3) */
+                         solve of a refinement step reduces the residual
+                         (scaled max norm); 0 = library choice (1e-1) */
   int max_outer;      /* mixed mode: refinement steps (per level-set band);
                          0 = library choice (30) */
   int band_bits;      /* mixed mode: when the coarse distance estimate puts

@@ -1,0 +1,125 @@
+"""Full-size workloads in the bench's launch configuration (mixed precision,
+componentwise tolerance 1e-6), checked through properties that hold at any
+size, and a sample of the full batched workload against the oracle.
+
+The property: each non-source row of the discrete system divided by phi_i
+(Sec. 4 Eq. phiEquation with the 5/7-point Laplacian of Sec. 6) reads
+    c sum_j omega_ij (exp((S_i - S_j)/hbar) - 1) = w_i f_i^2,
+so its defect divided by a_i, evaluated from S alone, is the componentwise
+residual of phi = exp(-S/hbar); with S exact at the sources it bounds the
+error of S.  It is evaluated here directly on the grid arrays (numpy), at
+the full sizes where the assembled oracle would be slow.
+"""
+import numpy as np
+import pytest
+
+from oracle import fd
+from paper_1403_1937_gb300 import workloads as wl
+
+
+@pytest.fixture(scope="module")
+def eik():
+    import torch
+    from paper_1403_1937_gb300 import build
+    build.build()
+    from paper_1403_1937_gb300 import eik as e
+    assert torch.cuda.is_available()
+    return e
+
+
+def identity_defect(S, f, dims, h, hbar, src):
+    """Row defects / a_i of the log-domain identity on every node (sources
+    set to 0).  S, f: arrays of shape dims[::-1] (x fastest)."""
+    c = hbar * hbar / (h * h)
+    nd = len(dims)
+    shape = S.shape
+    face = []
+    for ax in range(nd):          # ax 0 = x = last array axis
+        v = np.ones(dims[ax])
+        v[0] = v[-1] = 0.5
+        sh = [1] * nd
+        sh[nd - 1 - ax] = dims[ax]
+        face.append(v.reshape(sh))
+    w = np.ones(shape)
+    for v in face:
+        w = w * v
+    lhs = np.zeros(shape)
+    om_sum = np.zeros(shape)
+    for ax in range(nd):
+        a = nd - 1 - ax
+        om = np.ones(shape)
+        for b in range(nd):
+            if b != ax:
+                om = om * face[b]
+        lo = [slice(None)] * nd
+        hi = [slice(None)] * nd
+        lo[a] = slice(0, -1)
+        hi[a] = slice(1, None)
+        lo, hi = tuple(lo), tuple(hi)
+        diff = (S[lo] - S[hi]) / hbar
+        lhs[lo] += c * om[lo] * np.expm1(diff)
+        lhs[hi] += c * om[hi] * np.expm1(-diff)
+        om_sum[lo] += om[lo]
+        om_sum[hi] += om[hi]
+    a_diag = w * f * f + c * om_sum
+    d = (lhs - w * f * f) / a_diag
+    d.reshape(-1)[src] = 0.0
+    return d
+
+
+def solve(eik, inst, tol=1e-6):
+    import torch
+    opt = eik.make_options(precision="mixed", tol=tol)
+    f = torch.from_numpy(np.ascontiguousarray(inst.f)).cuda()
+    h = eik.eik_create(inst.dims, inst.h, inst.hbar, f, inst.src_idx, None, opt)
+    S, _, stats = eik.eik_solve(h)
+    eik.eik_destroy(h)
+    return S.cpu().numpy(), stats
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("cfg", ["c2", "c3"])
+def test_full_size_identity_residual(eik, cfg):
+    inst = wl.config2() if cfg == "c2" else wl.config3()
+    S, stats = solve(eik, inst)
+    S = S.reshape(inst.dims[::-1])
+    d = identity_defect(S, inst.f, inst.dims, inst.h, inst.hbar, inst.src_idx)
+    assert stats["res_cw"] <= 1e-6
+    assert np.max(np.abs(d)) <= 2e-6
+    Sf = S.reshape(-1)
+    assert np.all(Sf[inst.src_idx] == 0.0)
+    assert np.all(Sf >= 0.0) and np.all(np.isfinite(Sf))
+
+
+def test_identity_defect_matches_oracle_small():
+    """The grid form above against the oracle's assembled form (CPU only)."""
+    inst = wl.random_small(77, ndim=3, max_side=14, min_side=5)
+    S, _, sys = fd.solve(inst.f, inst.dims, inst.h, inst.hbar, inst.src_idx)
+    d = identity_defect(S.reshape(inst.dims[::-1]), inst.f, inst.dims, inst.h, inst.hbar,
+                        inst.src_idx)
+    S2 = S + 1e-3 * np.sin(np.arange(S.size))          # a perturbed S
+    S2[sys.src] = S[sys.src]
+    d2 = identity_defect(S2.reshape(inst.dims[::-1]), inst.f, inst.dims, inst.h, inst.hbar,
+                         inst.src_idx)
+    assert np.max(np.abs(d)) <= 1e-11
+    np.testing.assert_allclose(d2.reshape(-1)[sys.unk], fd.identity_residual(sys, S2),
+                               rtol=1e-9, atol=1e-13)
+
+
+@pytest.mark.gpu
+def test_full_batch_sample_vs_oracle(eik):
+    """Six instances of the full 256-instance batched workload (both ends of
+    the size range, each hbar/h, including ones that need the level-set
+    sweep), solved together through the batch API."""
+    insts = wl.config4()
+    pick = [43, 132, 5, 0, 2, 84]
+    sub = [insts[k] for k in pick]
+    opt = eik.make_options(precision="mixed", tol=1e-6)
+    b = eik.eik_create_batch(sub, opt)
+    S, stats = eik.eik_solve_batch(b)
+    parts = b.split(S.cpu().numpy())
+    for k, inst, Si in zip(pick, sub, parts):
+        sys = fd.assemble(inst.f, inst.dims, inst.h, inst.hbar, inst.src_idx)
+        S_ref = fd.solve_relative(sys)
+        assert np.max(np.abs(Si.ravel() - S_ref)) <= 1e-6, k
+    eik.eik_destroy_batch(b)
