@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--c4-count", type=int, default=256,
                     help="instances in the batched workload (c4)")
     ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--workers", type=int, default=0,
+                    help="batched workload: host worker threads driving the instances "
+                         "(eik_batch_set_concurrency); 0 library choice")
     ap.add_argument("--inner-tol", type=float, default=0.0,
                     help="mixed mode first inner-solve reduction (eik_options.inner_tol); "
                          "0 library choice")
@@ -326,7 +329,7 @@ def run_batch(args):
     opt = eik.make_options(precision=args.precision, tol=args.tol,
                            tile_override=args.tile_override, band_bits=args.band_bits,
                            inner_tol=args.inner_tol)
-    b = eik.eik_create_batch(insts, opt)
+    b = eik.eik_create_batch(insts, opt, workers=args.workers)
     S = torch.empty(b.n, dtype=torch.float64, device="cuda")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
