@@ -18,4 +18,6 @@ closed_forms  exact 1D-reducible discrete solution, lattice Green's function
               with mirror images, continuum Green's functions.
 cg            plain FP64 Jacobi-PCG on the assembled CSR matrix, in C with
               OpenMP (large grids and the timed CPU baseline).
+paths         nodal gradient of S and Euler backtracking of optimal paths
+              (path-planning section, Eq. PathPlanning-backTrackOnS).
 """
