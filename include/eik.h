@@ -245,6 +245,45 @@ eik_status eik_residual_noalloc(int ndim, const int64_t *dims, double h, double 
                                 int64_t nsrc, int boundary, double *res_max,
                                 eik_stream_t stream);
 
+/*
+ * Nodal gradient of S for path planning (path-planning section; the
+ * gradient descent on S that Eq. PathPlanning-backTrackOnS integrates).
+ * Component a of grad S at node i is (S[i+e_a] - S[i-e_a]) / (2h) inside the
+ * grid and the one-sided difference on the two faces of axis a.
+ *   dims   host array of ndim sizes (x first), each >= 2.
+ *   S      device, N doubles (C order, x fastest), e.g. from eik_solve.
+ *   gradS  device, ndim * N doubles, caller-owned; component a (x, y, z)
+ *          at gradS + a * N.
+ * Queued on `stream` and not awaited.  EIK_ERR_ARG for bad sizes, h <= 0 or
+ * null pointers; EIK_ERR_CUDA if the launch fails.
+ */
+eik_status eik_grad_S(int ndim, const int64_t *dims, double h, const double *S, double *gradS,
+                      eik_stream_t stream);
+
+/*
+ * Backtracking of optimal paths (path-planning section,
+ * Eq. PathPlanning-backTrackOnS): from each start point, explicit Euler
+ * steps of arc length `step` along -g/|g|, g the multilinear interpolation of
+ * gradS in the cell holding the point; points are clamped to the grid box
+ * [0, (n_a - 1) h].  Before every step a path stops if it lies within `eps`
+ * of a source node (status 0) or if |g| is zero or not finite (status 2);
+ * after max_steps steps it stops with status 1 (0 if then within eps).
+ *   gradS    device, from eik_grad_S.
+ *   starts   device, npaths * ndim doubles, world coordinates x = i h.
+ *   src_idx  device, nsrc flat node indices of the sources.
+ *   paths    device, npaths * (max_steps + 1) * ndim doubles, caller-owned:
+ *            point k of path p at paths + (p * (max_steps + 1) + k) * ndim;
+ *            points after the last are NaN.
+ *   lengths  device, npaths ints: steps taken (points = lengths + 1).
+ *   status   device, npaths ints (0 reached, 1 step limit, 2 flat gradient).
+ * One GPU thread per path, queued on `stream` and not awaited.  EIK_ERR_ARG
+ * for bad sizes, step <= 0, eps < 0, max_steps < 0 or null pointers.
+ */
+eik_status eik_backtrack(int ndim, const int64_t *dims, double h, const double *gradS,
+                         const double *starts, int64_t npaths, double step, int max_steps,
+                         const int64_t *src_idx, int64_t nsrc, double eps, double *paths,
+                         int *lengths, int *status, eik_stream_t stream);
+
 /* Per-kernel counters of a handle (diagnostics; the paper has no
  * counterpart).  launches counts every kernel launch the handle issued since
  * creation or the last eik_reset_kernel_stats (kernels inside captured graphs

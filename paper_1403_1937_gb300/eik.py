@@ -337,6 +337,52 @@ def eik_residual_noalloc(dims: Sequence[int], h: float, hbar: float, f, S, src_i
                                 "nodes; pointers must be device pointers)")
 
 
+def grad_S(S, dims: Sequence[int], h: float, stream=None):
+    """Nodal gradient of S (C: ``eik_grad_S``): a CUDA float64 tensor of
+    shape (ndim, N), component a = dS/dx_a."""
+    import torch
+    dims = tuple(int(d) for d in dims)
+    if not (_is_torch(S) and S.is_cuda):
+        raise TypeError("S must be a CUDA tensor")
+    n = int(np.prod(dims))
+    G = torch.empty((len(dims), n), dtype=torch.float64, device=S.device)
+    sp, sk = _ptr(S, np.float64, "S")
+    gp, gk = _ptr(G, np.float64, "gradS")
+    darr = (ctypes.c_int64 * len(dims))(*dims)
+    st = _lib.load().eik_grad_S(len(dims), darr, float(h), sp, gp, _stream_ptr(stream))
+    if st != _lib.EIK_OK:
+        raise _lib.EikError(st, "eik_grad_S failed")
+    return G
+
+
+def backtrack(G, dims: Sequence[int], h: float, starts, src_idx, step: float,
+              max_steps: int, eps: float, stream=None):
+    """Optimal paths from the start points (world coordinates, shape
+    (P, ndim)) down the gradient G from ``grad_S`` (C: ``eik_backtrack``).
+    Returns CUDA tensors (paths (P, max_steps + 1, ndim), lengths (P,),
+    status (P,))."""
+    import torch
+    dims = tuple(int(d) for d in dims)
+    nd = len(dims)
+    dev = G.device
+    starts = torch.as_tensor(starts, dtype=torch.float64).reshape(-1, nd).to(dev).contiguous()
+    src = torch.as_tensor(np.asarray(src_idx, dtype=np.int64)).to(dev).contiguous()
+    P = starts.shape[0]
+    paths = torch.empty((P, int(max_steps) + 1, nd), dtype=torch.float64, device=dev)
+    lengths = torch.empty(P, dtype=torch.int32, device=dev)
+    status = torch.empty(P, dtype=torch.int32, device=dev)
+    darr = (ctypes.c_int64 * nd)(*dims)
+    gp, gk = _ptr(G, np.float64, "gradS")
+    st = _lib.load().eik_backtrack(
+        nd, darr, float(h), gp, ctypes.c_void_p(starts.data_ptr()), P, float(step),
+        int(max_steps), ctypes.c_void_p(src.data_ptr()), int(src.numel()), float(eps),
+        ctypes.c_void_p(paths.data_ptr()), ctypes.c_void_p(lengths.data_ptr()),
+        ctypes.c_void_p(status.data_ptr()), _stream_ptr(stream))
+    if st != _lib.EIK_OK:
+        raise _lib.EikError(st, "eik_backtrack failed")
+    return paths, lengths, status
+
+
 def solve(f, h: float, hbar: float, src_idx, src_U=None, precision: str = "fp64",
           tol: Optional[float] = None, want_phi: bool = False, **kw):
     """One-shot convenience: dims are taken from the array shape (numpy order
