@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"])
     ap.add_argument("--c4-count", type=int, default=256,
                     help="instances in the batched workload (c4)")
     ap.add_argument("--tol", type=float, default=1e-6)
@@ -306,6 +306,93 @@ def run_ours(args):
     return inst, desc, n_unk, results, ws, rank
 
 
+def run_diff(args):
+    """Differentiation workload (config 5): 32 instances of 512^2, one source
+    each; a step is the forward solve of the batch, dL/dS = 2 (S - T) on 4096
+    receivers per instance, and the adjoint solve giving dL/df.  The targets
+    T = S_ref + noise come from a solve of the separately seeded reference
+    fields with this library (synthetic input data, made before timing)."""
+    import torch
+    from paper_1403_1937_gb300 import build as _build
+    if not _build.up_to_date():
+        _build.build()
+    from paper_1403_1937_gb300 import eik
+    from paper_1403_1937_gb300 import workloads as wl
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    data = wl.config5()
+    mine = shard_instances([d[0].n for d in data], ws)[rank]
+    data = [data[k] for k in mine]
+    insts = [d[0] for d in data]
+    opt = eik.make_options(precision=args.precision, tol=args.tol,
+                           tile_override=args.tile_override, band_bits=args.band_bits,
+                           inner_tol=args.inner_tol)
+    b = eik.eik_create_batch(insts, opt, workers=args.workers)
+    offs = np.cumsum([0] + [i.n for i in insts])
+    # targets from the reference fields
+    f_ref = torch.from_numpy(np.concatenate([d[2].ravel() for d in data])).cuda()
+    eik.eik_set_f_batch(b, f_ref)
+    S_ref, _ = eik.eik_solve_batch(b)
+    recv = torch.from_numpy(np.concatenate([d[1] + offs[k] for k, d in enumerate(data)])).cuda()
+    noise = torch.from_numpy(np.concatenate([d[3] for d in data])).cuda()
+    T = S_ref[recv] + noise
+    f_all = torch.from_numpy(np.concatenate([i.f.ravel() for i in insts])).cuda()
+    n_unk = [i.n - len(np.unique(i.src_idx)) for i in insts]
+    S = torch.empty(b.n, dtype=torch.float64, device="cuda")
+    dLdS = torch.zeros(b.n, dtype=torch.float64, device="cuda")
+    dLdf = torch.empty(b.n, dtype=torch.float64, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def step():
+        eik.eik_set_f_batch(b, f_all)
+        _, st_f = eik.eik_solve_batch(b, S_out=S)
+        dLdS.index_copy_(0, recv, 2.0 * (S[recv] - T))
+        _, st_a = eik.eik_grad_batch(b, dLdS, dLdf_out=dLdf)
+        return st_f, st_a
+
+    for _ in range(args.warmup):
+        step()
+    times, units, fwd_it, adj_it = [], 0, 0, 0
+    with Clocks(local) as clk:
+        for _ in range(args.steps):
+            flush_l2(flush)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st_f, st_a = step()
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+            fwd_it += sum(s_["inner_iters"] for s_ in st_f)
+            adj_it += sum(s_["inner_iters"] for s_ in st_a)
+            units += sum(u * (a["inner_iters"] + c["inner_iters"])
+                         for u, a, c in zip(n_unk, st_f, st_a))
+    total, units = job_totals(sum(times), units, ws, "cuda")
+    if rank != 0:
+        return
+    loss = float(((S[recv] - T) ** 2).sum())
+    line = {"metric": METRIC, "value": round(units / total / 1e9, 4), "unit": UNIT,
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * total / args.steps, 3), "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64 forward, f64 adjoint",
+            "data": "synthetic",
+            "config": {"workload": "differentiation: 32 x 512^2 Fourier f, 1 source, hbar=0.01, "
+                                   "4096 receivers each; forward + adjoint solve per step",
+                       "instances": 32, "instances_rank0": len(insts),
+                       "precision": args.precision, "tol_componentwise": args.tol,
+                       "l2": "flushed between steps (256 MiB write)"},
+            "clocks": clk.summary(),
+            "iterations_per_step": {"forward": fwd_it / args.steps,
+                                    "adjoint": adj_it / args.steps},
+            "loss": loss}
+    print(json.dumps(line), flush=True)
+
+
 def run_batch(args):
     """Batched workload: independent 2D instances of uneven size, f, sources
     and hbar (config 4), solved together through eik_solve_batch."""
@@ -440,6 +527,9 @@ def main():
         return
     if args.workload == "c4":
         run_batch(args)
+        return
+    if args.workload == "c5":
+        run_diff(args)
         return
     inst, desc, n_unk, results, ws, rank = run_ours(args)
     if rank != 0:

@@ -1221,6 +1221,16 @@ k_mixed2d_tma(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ 
   for (int t = first; t < ntiles; t += step, ++k) {
     const int stg = k % NS;
     const uint32_t parity = (uint32_t)(k / NS) & 1u;
+    // pass 2: the cell exponent of the warp's first row, loaded before the
+    // wait so its latency hides behind it (reloaded below only when the row
+    // crosses into the next cell row)
+    int kcy = -1, kyi = 0;
+    if (PASS2) {
+      const int xq = min((t % tiles_x) * kTmaTX + 64 * cw + 2 * lane, g.nx - 1);
+      const int yq = min((t / tiles_x) * TY + rg * RW, g.ny - 1);
+      kcy = yq >> cg.lgB;
+      kyi = kx[(xq >> cg.lgB) + cg.cx * kcy];
+    }
     const bool ok = mbar_wait_bounded(&bar[stg], parity);
     if (__syncthreads_or(!ok)) {
       fault = true;
@@ -1277,7 +1287,10 @@ k_mixed2d_tma(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ 
           const float2 dd = *reinterpret_cast<const float2 *>(S + T::OFF_D + 4 * li);
           float2 xr = make_float2(0.f, 0.f);
           if (want_x) xr = *reinterpret_cast<const float2 *>(S + T::OFF_X + 4 * li);
-          const int kyi = kx[(x >> cg.lgB) + cg.cx * (y >> cg.lgB)];   // x, x+1: one cell
+          if ((y >> cg.lgB) != kcy) {   // x, x+1: one cell
+            kcy = y >> cg.lgB;
+            kyi = kx[(x >> cg.lgB) + cg.cx * kcy];
+          }
           float d[2] = {dd.x, dd.y}, rn[2], pn[2];
           int en[2];
           const float pt[2] = {C.pt0, C.pt1}, rr[2] = {C.r0, C.r1}, q[2] = {q0, q1};
@@ -1479,6 +1492,7 @@ k_mixed3d_tma(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ 
     const int x = xt * kTmaTX + lc, y = (rest % tiles_y) * TY + ry;
     const int z0 = (rest / tiles_y) * zc;
     const int q0 = k * PL;
+    int kcz = -1, kyi = 0;   // cell exponent of (x, y, z), cached per cell in z
     const float wyz = (half && (y == 0 || y == g.ny - 1)) ? 0.5f : 1.f;   // hy
     const float hx0 = (half && x == 0) ? 0.5f : 1.f;
     const float hx1 = (half && x + 1 == g.nx - 1) ? 0.5f : 1.f;
@@ -1545,7 +1559,10 @@ k_mixed3d_tma(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ 
           const float2 dd = *reinterpret_cast<const float2 *>(Sc + T::OFF_D + 4 * li);
           float2 xr = make_float2(0.f, 0.f);
           if (want_x) xr = *reinterpret_cast<const float2 *>(Sc + T::OFF_X + 4 * li);
-          const int kyi = kx[cell_of(cg, x, y, z)];   // x, x+1: one cell
+          if ((z >> cg.lgB) != kcz) {   // x, x+1: one cell; y fixed per warp
+            kcz = z >> cg.lgB;
+            kyi = kx[cell_of(cg, x, y, z)];
+          }
           float d[2] = {dd.x, dd.y}, rn[2], pn[2];
           int en[2];
           const float pt[2] = {C.pt0, C.pt1}, rr[2] = {C.r0, C.r1}, qq[2] = {q0v, q1v};
