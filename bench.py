@@ -133,11 +133,18 @@ def measured_peaks():
 
 
 def kernel_source_hash(files):
+    """Hash of the kernel sources with comments and whitespace removed, so a
+    comment edit does not void the recorded ncu counters but any code change
+    does."""
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1403_1937_gb300", "csrc")
     for name in files:
-        with open(os.path.join(csrc, name), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(csrc, name), encoding="utf-8") as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

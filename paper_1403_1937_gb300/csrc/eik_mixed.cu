@@ -17,13 +17,25 @@
 // All rescaling is by powers of two, so it is exact; CG arithmetic is that of
 // Jacobi-preconditioned CG on the scaled operator Ahat (see eik_internal.cuh)
 // rounded to FP32 mantissas.  Inner products are accumulated as
-// (mantissa, exponent) pairs so they cannot underflow or overflow.
+// (mantissa, exponent) pairs (or, in the TMA kernels, in FP32 relative to the
+// previous <rhat, rhat>) so they cannot underflow or overflow.
 //
 // The inner FP32 CG yields accurate values near the sources but not in the
 // far field: CG iterates there pass through transients many orders larger
 // than the final values, whose cancellation FP32 cannot carry.  Refinement
 // repairs this: each outer step forms the true FP64 residual in relative
 // form and solves for a correction with a fresh inner CG.
+//
+// When kx spans more than a few hundred powers of two, no global CG (in any
+// precision) resolves the far field: its transients there exceed even the
+// FP32 exponent range of the correction.  The solve then sweeps level-set
+// bands of kx, nearest first, each refined with the rest of the grid held as
+// Dirichlet data (mixed_solve / refine).
+//
+// Inner-CG kernels: TMA-staged tiles with mbarrier pipelines on sm_103a
+// (k_mixed2d_tma, k_mixed3d_tma) where the row pitch allows 16-byte aligned
+// tensor maps, warp-marched rows (k_mixed2d) or generic halo tiles
+// (k_mixed_pass1/2) elsewhere.
 #include <cuda.h>
 #include <math.h>
 #include <stdio.h>
@@ -714,8 +726,8 @@ k_mixed_pass2(Grid g, TileCount tc, CellGrid cg, const int *__restrict__ kx,
 // ------------------------------------------- 2D inner CG, warp-marched rows
 // Specialisation for 2D grids with nx % VEC == 0: a warp owns 32*VEC
 // consecutive columns (VEC = 2 or 4 per lane, vector loads) and marches down
-// kRowsPerWarp rows,
-// keeping the rows above and below in registers and taking the x neighbours
+// kRowsPerWarp rows, keeping the rows above and below in registers and taking
+// the x neighbours
 // by warp shuffle (lanes 0 and 31 load the column beyond the warp).  No shared
 // memory and no block barrier on the data path; the next row's loads are
 // issued before the current row is computed.  Arithmetic is that of
