@@ -118,7 +118,13 @@ typedef struct {
                          two (nearest first, half a band of overlap), holding
                          the rest as Dirichlet data; 0 = library choice (48),
                          negative = never sweep */
-  int reserved[6];
+  int test_flags;     /* test hook, 0 in normal use.  Bit 0 (mixed mode, 2D
+                         TMA kernels): one block of the inner CG's first
+                         pass never gets its first tile copy, so its bounded
+                         wait (0.2 s) expires and the solve returns
+                         EIK_ERR_TIMEOUT; exercises the timeout path without
+                         any fault. */
+  int reserved[5];
 } eik_options;
 
 typedef struct {

@@ -39,7 +39,8 @@ class Options(ctypes.Structure):
                 ("stop_norm", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("boundary", ctypes.c_int), ("tile_override", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
-                ("band_bits", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+                ("band_bits", ctypes.c_int), ("test_flags", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
 
 
 class Stats(ctypes.Structure):

@@ -61,7 +61,7 @@ def make_options(precision: str = "fp64", tol: Optional[float] = None,
                  stop_norm: str = "componentwise", max_iter: Optional[int] = None,
                  boundary: str = "half_cell", inner_tol: float = 0.0,
                  max_outer: int = 0, tile_override: int = 0,
-                 band_bits: int = 0) -> _lib.Options:
+                 band_bits: int = 0, test_flags: int = 0) -> _lib.Options:
     o = _lib.default_options()
     o.precision = {"fp64": _lib.PREC_FP64, "mixed": _lib.PREC_MIXED}[precision]
     if tol is not None:
@@ -76,6 +76,7 @@ def make_options(precision: str = "fp64", tol: Optional[float] = None,
     o.max_outer = int(max_outer)
     o.tile_override = int(tile_override)
     o.band_bits = int(band_bits)
+    o.test_flags = int(test_flags)
     return o
 
 

@@ -145,3 +145,43 @@ def test_band_width_does_not_change_the_solution(eik, band_bits):
     S_ref, _, _ = fd.solve(inst.f, inst.dims, inst.h, inst.hbar, inst.src_idx)
     assert np.max(np.abs(S - S_ref)) <= S_ABS
     assert stats["res_cw"] <= 1e-8
+
+
+def test_bounded_wait_timeout_is_reported(eik):
+    """Failure detection without a fault: with test_flags bit 0 one block of
+    the first TMA pass never gets its tile copy; its bounded wait expires,
+    the kernel sets the fault flag, waits (bounded) for its own copies in
+    flight and returns; the solve reports EIK_ERR_TIMEOUT and the GPU context
+    stays usable for the next solve."""
+    import torch
+    from paper_1403_1937_gb300 import _lib
+    inst = wl.config2(n=256)
+    f = torch.from_numpy(inst.f).cuda()
+    opt = eik.make_options(precision="mixed", tol=1e-6, test_flags=1)
+    h = eik.eik_create(inst.dims, inst.h, inst.hbar, f, inst.src_idx, None, opt)
+    with pytest.raises(_lib.EikError) as ei:
+        eik.eik_solve(h)
+    assert ei.value.status == _lib.EIK_ERR_TIMEOUT
+    assert "timed out" in str(ei.value)
+    eik.eik_destroy(h)
+    S, _, stats, _ = mixed_solve(eik, inst, tol=1e-8)
+    S_ref, _, _ = fd.solve(inst.f, inst.dims, inst.h, inst.hbar, inst.src_idx)
+    assert np.max(np.abs(S - S_ref)) <= S_ABS
+
+
+@pytest.mark.parametrize("ndim,tile_override", [
+    (2, 1), (2, 2), (2, 3), (2, 4), (2, 5), (2, 6), (2, 7), (2, 10), (2, 11), (2, 12),
+    (3, 1), (3, 8), (3, 9)])
+def test_kernel_variants_agree_with_oracle(eik, ndim, tile_override):
+    """Every inner-CG kernel variant (generic halo tiles, warp-marched rows,
+    TMA-staged tiles of each shape and depth, 3D z-marching) meets the S
+    bound on a grid whose nx admits all of them."""
+    inst = wl.config2(n=264) if ndim == 2 else wl.config3(n=40)
+    import torch
+    opt = eik.make_options(precision="mixed", tol=1e-9, tile_override=tile_override)
+    f = torch.from_numpy(np.ascontiguousarray(inst.f)).cuda()
+    h = eik.eik_create(inst.dims, inst.h, inst.hbar, f, inst.src_idx, None, opt)
+    S, _, stats = eik.eik_solve(h)
+    eik.eik_destroy(h)
+    S_ref, _, _ = fd.solve(inst.f, inst.dims, inst.h, inst.hbar, inst.src_idx)
+    assert np.max(np.abs(S.cpu().numpy().ravel() - S_ref)) <= S_ABS
