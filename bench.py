@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--c4-count", type=int, default=256,
                     help="instances in the batched workload (c4)")
     ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--per-launch", action="store_true",
+                    help="launch every inner iteration on its own instead of in CUDA graphs "
+                         "(no launches past convergence; for profiler captures, not for timing)")
     ap.add_argument("--workers", type=int, default=0,
                     help="batched workload: host worker threads driving the instances "
                          "(eik_batch_set_concurrency); 0 library choice")
@@ -255,6 +258,8 @@ def run_ours(args):
         except Exception as e:  # mixed may be unavailable in this build
             results[mode] = {"error": str(e).splitlines()[0]}
             continue
+        if args.per_launch:
+            eik.eik_set_profiling(hd, True)
         for _ in range(args.warmup):
             eik.eik_set_f(hd, f_dev)
             eik.eik_solve(hd, S_out=S_dev)
