@@ -34,8 +34,8 @@ if ROOT not in sys.path:
 METRIC = "stencil-PCG GLUPS and solve time, mixed vs FP64 plain at S err<=1e-6; %HBM peak"
 UNIT = "GLUPS"
 
-# Algorithmic bytes per grid node for one launch of each CG kernel
-# ("Kernels and their rooflines").
+# Algorithmic bytes per grid node for one launch of each CG kernel: every
+# array the kernel must read or write, counted once per node.
 ALGO_BYTES_PER_NODE = {
     "cg_pass1_64": 32,   # read r, p, sig; write q            (4 x 8 B)
     "cg_pass2_64": 56,   # read x, r, p, q; write x, r, p     (7 x 8 B)

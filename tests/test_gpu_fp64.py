@@ -1,6 +1,6 @@
 """FP64 CUDA path vs the CPU oracle, through the C ABI.
 
-Bar (spec tolerances): phi pointwise relative error <= 1e-10 and
+Bar: phi pointwise relative error <= 1e-10 and
 S absolute error <= 1e-6 against the oracle's direct (or tight CG) solution.
 """
 import numpy as np

@@ -1,7 +1,7 @@
 """Mixed-precision path (FP32 block-floating-point inner CG + FP64 iterative
 refinement) vs the CPU oracle, through the C ABI.
 
-Bar (the benchmark spec): S absolute error <= 1e-6 against the FP64 oracle, on every
+Bar: S absolute error <= 1e-6 against the FP64 oracle, on every
 config, including problems whose phi underflows float64 (S/hbar > 700), where
 the oracle uses its relative-form direct solve.
 """
