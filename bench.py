@@ -43,6 +43,16 @@ ALGO_BYTES_PER_NODE = {
     "mixed_pass2": 32,   # read r, p, e, sig, d; write r, p, e (other set), d
 }
 
+# The FP64 passes are bound by the FP64 pipe, not by HBM: their roofline is
+# algorithmic FP64 operations (an FMA counts 2) per node against the GB300's
+# FP64 rate, 152 SMs x 2.07 GHz x 4 FP64 FLOP/clock = 1.26 TFLOP/s (nominal
+# 1.25).  Pass 1: ptil = r + beta p (FMA), u = sig ptil, the 4 (6) neighbour
+# additions, q = ptil - sig sum (FMA), <ptil, q> (FMA): 10 FLOP in 2D, 12 in
+# 3D.  Pass 2: ptil, x, r updates and <r, r> (4 FMA): 8 FLOP.
+FP64_PEAK_TFLOPS = 1.25
+ALGO_FLOPS_PER_NODE = {("cg_pass1_64", 2): 10, ("cg_pass1_64", 3): 12,
+                       ("cg_pass2_64", 2): 8, ("cg_pass2_64", 3): 8}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -476,9 +486,21 @@ def roofline(res, inst, wname):
         return None
     dom = max(cand, key=lambda k: cand[k][2])
     avg_ms = cand[dom][0]
+    total = sum(v[2] for v in km.values())
+    if dom.startswith("cg_"):
+        flops = ALGO_FLOPS_PER_NODE[(dom, len(inst.dims))] * inst.n
+        achieved = flops / (avg_ms * 1e-3) / 1e12
+        return {"bound": "alu", "kernel": dom, "achieved": round(achieved, 4),
+                "peak": FP64_PEAK_TFLOPS,
+                "peak_source": "nominal FP64 rate (152 SMs x 2.07 GHz x 4 FLOP/clock)",
+                "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
+                "traffic": ncu_traffic(dom, wname),
+                "algorithmic_flops_per_launch": flops,
+                "algorithmic_bytes_per_launch": ALGO_BYTES_PER_NODE[dom] * inst.n,
+                "avg_launch_ms": avg_ms,
+                "share_of_kernel_time": round(cand[dom][2] / total, 3) if total else None}
     algo = ALGO_BYTES_PER_NODE[dom] * inst.n
     achieved = algo / (avg_ms * 1e-3) / 1e9
-    total = sum(v[2] for v in km.values())
     return {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
             "peak": peak, "peak_source": peak_src, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": ncu_traffic(dom, wname),
