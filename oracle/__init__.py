@@ -20,4 +20,6 @@ cg            plain FP64 Jacobi-PCG on the assembled CSR matrix, in C with
               OpenMP (large grids and the timed CPU baseline).
 paths         nodal gradient of S and Euler backtracking of optimal paths
               (path-planning section, Eq. PathPlanning-backTrackOnS).
+sfs           shape-from-shading forcing f = sqrt(1/P^2 - 1)
+              (Eq. SfS-forcingFunc).
 """

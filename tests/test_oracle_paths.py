@@ -98,3 +98,23 @@ def test_backtracking_descends_the_discrete_solution():
     for p in range(len(starts)):
         s = paths.interp(Sg, inst.dims, inst.h, P[p, :L[p] + 1])[:, 0]
         assert np.all(np.diff(s) <= 1e-12)
+
+
+# ---- shape-from-shading forcing (Eq. SfS-forcingFunc)
+from oracle import sfs   # noqa: E402
+
+
+def test_sfs_forcing_inverts_the_imaging_operator():
+    """f = sqrt(1/P^2 - 1) returns |grad S*| for P = 1/sqrt(|grad S*|^2 + 1),
+    checked on the analytic gradient of a paraboloid; f_min clamps flat
+    points; P outside (0, 1] is rejected as NaN."""
+    x = np.linspace(-1, 1, 41)
+    X, Y = np.meshgrid(x, x)
+    gz = np.sqrt((2 * 0.7 * X) ** 2 + (2 * 0.7 * Y) ** 2)     # |grad| of 0.7 (x^2 + y^2)
+    P = sfs.image_of_height(gz ** 2)
+    f = sfs.forcing(P, 0.0)
+    assert np.max(np.abs(f - gz)) <= 1e-12
+    f2 = sfs.forcing(P, 0.05)
+    assert np.all(f2 >= 0.05) and np.allclose(f2[gz > 0.05], gz[gz > 0.05], atol=1e-12)
+    bad = sfs.forcing(np.array([0.0, -0.1, 1.5, np.nan, 1.0]), 0.01)
+    assert np.all(np.isnan(bad[:4])) and bad[4] == 0.01
