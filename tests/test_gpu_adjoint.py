@@ -103,3 +103,28 @@ def test_backward_after_second_forward_is_rejected(mods):
     with pytest.raises(RuntimeError):
         S1.sum().backward()
     layer.close()
+
+
+@pytest.mark.slow
+def test_full_size_c5_gradient_vs_oracle(mods):
+    """One instance of the differentiation workload at its full size (512^2,
+    4096 receivers): forward in mixed precision, hand-written adjoint, against
+    the oracle's gradient through the same factorisation."""
+    torch, autograd, eik = mods
+    inst, recv, f_ref, eps = wl.config5(count=1)[0]
+    S_ref, _, _ = fd.solve(f_ref, inst.dims, inst.h, inst.hbar, inst.src_idx)
+    T = S_ref[recv] + eps
+    layer = autograd.Eikonal(inst.dims, inst.h, inst.hbar, inst.src_idx, precision="mixed",
+                             tol=1e-9)
+    f = torch.from_numpy(inst.f).cuda().requires_grad_(True)
+    S = layer(f)
+    recv_t = torch.from_numpy(recv).cuda()
+    L = ((S.reshape(-1)[recv_t] - torch.from_numpy(T).cuda()) ** 2).sum()
+    L.backward()
+    g = f.grad.cpu().numpy().ravel()
+    S_o, _, sys = fd.solve(inst.f, inst.dims, inst.h, inst.hbar, inst.src_idx)
+    dLdS = np.zeros(sys.n)
+    dLdS[recv] = 2.0 * (S_o[recv] - T)
+    g_ref = fd.grad_f(sys, dLdS)
+    assert np.max(np.abs(g - g_ref)) <= 1e-6 * np.max(np.abs(g_ref))
+    layer.close()
