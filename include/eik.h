@@ -290,6 +290,21 @@ eik_status eik_backtrack(int ndim, const int64_t *dims, double h, const double *
                          const int64_t *src_idx, int64_t nsrc, double eps, double *paths,
                          int *lengths, int *status, eik_stream_t stream);
 
+/*
+ * Shape-from-shading forcing (shape-from-shading section, Eq.
+ * SfS-forcingFunc): for a Lambertian image under vertical light,
+ * P = 1/sqrt(|grad S|^2 + 1), the height field S solves the eikonal equation
+ * with f = sqrt(1/P^2 - 1); seed eik_create with known heights as source
+ * values U.  f is raised to f_min where the formula gives less (flat image
+ * regions give 0, which eik_create rejects); P outside (0, 1] or not finite
+ * yields NaN there (also rejected by eik_create).
+ *   P, f   device, n doubles each (f caller-owned).
+ * Queued on `stream`, not awaited.  EIK_ERR_ARG for n < 0, f_min < 0 or null
+ * pointers with n > 0.
+ */
+eik_status eik_sfs_forcing(const double *P, int64_t n, double f_min, double *f,
+                           eik_stream_t stream);
+
 /* Per-kernel counters of a handle (diagnostics; the paper has no
  * counterpart).  launches counts every kernel launch the handle issued since
  * creation or the last eik_reset_kernel_stats (kernels inside captured graphs

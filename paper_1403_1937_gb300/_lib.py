@@ -96,6 +96,7 @@ _SIGS = [
     ("eik_backtrack", ctypes.c_int,
      [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_double, _P, _P, ctypes.c_int64,
       ctypes.c_double, ctypes.c_int, _P, ctypes.c_int64, ctypes.c_double, _P, _P, _P, _P]),
+    ("eik_sfs_forcing", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double, _P, _P]),
     ("eik_last_error", ctypes.c_char_p, []),
     ("eik_abi_version", ctypes.c_int, []),
     ("eik_cuda_arch", ctypes.c_int, []),

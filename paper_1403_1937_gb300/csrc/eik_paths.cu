@@ -168,3 +168,35 @@ extern "C" eik_status eik_backtrack(int ndim, const int64_t *dims, double h, con
       d, h, gradS, starts, npaths, step, max_steps, src_idx, nsrc, eps, paths, lengths, status);
   return cudaGetLastError() == cudaSuccess ? EIK_OK : EIK_ERR_CUDA;
 }
+
+// Shape-from-shading forcing (shape-from-shading section, Eq. SfS-forcingFunc):
+// a Lambertian image under vertical light, P = 1/sqrt(|grad S|^2 + 1), gives
+// the eikonal forcing f = sqrt(1/P^2 - 1), raised to f_min where smaller
+// (flat regions would give f = 0, which eik_create rejects); P outside
+// (0, 1] or not finite gives NaN (eik_create rejects it).  Explicitly
+// rounded operations, as in the path kernels.
+namespace {
+__global__ void k_sfs_forcing(const double *__restrict__ P, int64_t n, double f_min,
+                              double *__restrict__ f) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double p = P[i];
+    double v = NAN;
+    if (p > 0.0 && p <= 1.0) {
+      const double g = __dsqrt_rn(__dsub_rn(__ddiv_rn(1.0, __dmul_rn(p, p)), 1.0));
+      v = fmax(g, f_min);
+    }
+    f[i] = v;
+  }
+}
+}  // namespace
+
+extern "C" eik_status eik_sfs_forcing(const double *P, int64_t n, double f_min, double *f,
+                                      eik_stream_t stream) {
+  if (n < 0 || !(f_min >= 0.0) || (n > 0 && (!P || !f))) return EIK_ERR_ARG;
+  if (n == 0) return EIK_OK;
+  const int th = 256;
+  const int nb = (int)std::min<int64_t>((n + th - 1) / th, 152 * 16);
+  k_sfs_forcing<<<nb, th, 0, stream>>>(P, n, f_min, f);
+  return cudaGetLastError() == cudaSuccess ? EIK_OK : EIK_ERR_CUDA;
+}

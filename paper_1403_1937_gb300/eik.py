@@ -384,6 +384,21 @@ def backtrack(G, dims: Sequence[int], h: float, starts, src_idx, step: float,
     return paths, lengths, status
 
 
+def sfs_forcing(P, f_min: float = 0.0, stream=None):
+    """Eikonal forcing of a shape-from-shading image (C: ``eik_sfs_forcing``):
+    f = max(sqrt(1/P^2 - 1), f_min) for a CUDA float64 tensor P."""
+    import torch
+    if not (_is_torch(P) and P.is_cuda):
+        raise TypeError("P must be a CUDA tensor")
+    f = torch.empty_like(P)
+    pp, pk = _ptr(P, np.float64, "P")
+    fp, fk = _ptr(f, np.float64, "f")
+    st = _lib.load().eik_sfs_forcing(pp, _numel(P), float(f_min), fp, _stream_ptr(stream))
+    if st != _lib.EIK_OK:
+        raise _lib.EikError(st, "eik_sfs_forcing failed")
+    return f
+
+
 def solve(f, h: float, hbar: float, src_idx, src_U=None, precision: str = "fp64",
           tol: Optional[float] = None, want_phi: bool = False, **kw):
     """One-shot convenience: dims are taken from the array shape (numpy order

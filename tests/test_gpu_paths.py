@@ -88,3 +88,42 @@ def test_backtrack_edge_cases(eik):
         eik.backtrack(G, dims, h, np.zeros((1, 2)), src, -1.0, 10, 0.2)
     with pytest.raises(_lib.EikError):
         eik.grad_S(torch.zeros(63, dtype=torch.float64).cuda(), (63,), h)
+
+
+def test_sfs_forcing_bitwise(eik):
+    import torch
+    from oracle import sfs
+    rng = np.random.default_rng(4)
+    P = np.concatenate([rng.uniform(1e-3, 1.0, 4093), [1.0, 0.0, -0.5, 1.5, np.nan]])
+    f = eik.sfs_forcing(torch.from_numpy(P).cuda(), 0.01).cpu().numpy()
+    np.testing.assert_array_equal(f, sfs.forcing(P, 0.01))
+
+
+def test_shape_from_shading_recovers_height(eik):
+    """A paraboloid height field z imaged under vertical light: the forcing
+    from the image, one seed at the minimum with its height, and the mixed
+    solve give the oracle's discrete solution (S within 1e-6) and a height
+    field whose distance to z shrinks with hbar (O(hbar) plus the source's
+    logarithmic term)."""
+    import torch
+    from oracle import fd, sfs
+    errs = []
+    for n in (129, 257):
+        h = 1.0 / (n - 1)
+        x = np.arange(n) * h
+        X, Y = np.meshgrid(x, x)
+        z = 0.7 * ((X - 0.5) ** 2 + (Y - 0.5) ** 2)
+        P = sfs.image_of_height((1.4 * (X - 0.5)) ** 2 + (1.4 * (Y - 0.5)) ** 2)
+        f = eik.sfs_forcing(torch.from_numpy(P.ravel()).cuda(), 1e-3)
+        src = np.array([(n // 2) * n + n // 2], dtype=np.int64)
+        hbar = 2 * h
+        opt = eik.make_options(precision="mixed", tol=1e-9)
+        hd = eik.eik_create((n, n), h, hbar, f, src, np.array([z.ravel()[src[0]]]), opt)
+        S, _, _ = eik.eik_solve(hd)
+        eik.eik_destroy(hd)
+        S = S.cpu().numpy().ravel()
+        S_ref, _, _ = fd.solve(sfs.forcing(P.ravel(), 1e-3), (n, n), h, hbar, src)
+        assert np.max(np.abs(S - S_ref)) <= 1e-6
+        errs.append(np.max(np.abs(S - z.ravel())))
+        assert errs[-1] <= 15 * hbar
+    assert errs[1] < 0.7 * errs[0]
