@@ -90,19 +90,21 @@ typedef struct {
   int boundary;       /* EIK_BOUNDARY_*; default half cell */
   int tile_override;  /* mixed-mode inner-CG kernel variant (results agree
                          to rounding; for tuning and tests):
-                         0 = library choice (nx % 8 == 0: TMA-staged tiles
-                             of 128 x 16 nodes in 2D, 128 x 4 rows marching
-                             in z in 3D; other even nx in 2D: warp-marched
-                             rows; otherwise generic);
+                         0 = library choice: TMA-staged tiles of 128 x 16
+                             nodes in 2D, 128 x 4 rows marching in z in 3D,
+                             when nx % 8 == 0 or the grid has >= 2^20 nodes
+                             (the FP32 arrays then get a row pitch rounded up
+                             to 8 for the tensor maps); otherwise warp-marched
+                             rows (2D, even nx) or generic kernels;
                          1 = generic halo-tile kernels everywhere;
                          2 / 3 = warp-marched rows, 4 / 2 columns per lane
                              (2D, nx divisible by that);
-                         4..7 = TMA-staged tiles (2D, nx % 8 == 0) with
+                         4..7 = TMA-staged tiles (2D) with
                              (rows per tile, warps per block) = (16, 4),
                              (32, 8), (16, 8), (32, 4);
-                         8 / 9 = TMA-staged z-marching tiles (3D,
-                             nx % 8 == 0) of 4 / 8 rows (3D default: 4);
-                         10..12 = TMA-staged tiles (2D, nx % 8 == 0) with
+                         8 / 9 = TMA-staged z-marching tiles (3D) of
+                             4 / 8 rows (3D default: 4);
+                         10..12 = TMA-staged tiles (2D) with
                              (rows, warps, pipeline stages) = (8, 8, 4),
                              (16, 8, 3), (8, 4, 4).
                          A variant whose condition fails falls back to the

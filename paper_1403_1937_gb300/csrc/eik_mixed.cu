@@ -227,23 +227,31 @@ __device__ __forceinline__ void tile_origin_m(const TileCount &tc, int64_t t, in
 }
 
 // ----------------------------------------------------------- setup kernels
-__global__ void k_sig32(int64_t n, const double *__restrict__ sig, float *__restrict__ s32) {
+// The FP32 / int16 inner-CG arrays use a row pitch px >= nx (a multiple of 8
+// where the TMA kernels run, so their rows are 16-byte aligned); the FP64
+// arrays are dense.  pidx maps a dense index to the pitched one.
+__device__ __forceinline__ int64_t pidx(int64_t i, int nx, int px) {
+  return (px == nx) ? i : (i / nx) * px + (i % nx);
+}
+
+__global__ void k_sig32(int64_t n, int nx, int px, const double *__restrict__ sig,
+                        float *__restrict__ s32) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    s32[i] = (float)sig[i];
+    s32[pidx(i, nx, px)] = (float)sig[i];
 }
 
 // s32 for one level-set band: sigma where band_lo <= kx(cell) < band_hi, 0
 // elsewhere (those nodes then act as Dirichlet data in the inner CG).
-__global__ void k_sig32_band(Grid g, CellGrid cg, const int *__restrict__ kx, int lo, int hi,
-                             const double *__restrict__ sig, float *__restrict__ s32) {
+__global__ void k_sig32_band(Grid g, int px, CellGrid cg, const int *__restrict__ kx, int lo,
+                             int hi, const double *__restrict__ sig, float *__restrict__ s32) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int x = (int)(i % g.nx);
     const int64_t t = i / g.nx;
     const int y = (int)(t % g.ny), z = (int)(t / g.ny);
     const int k = kx[cell_of(cg, x, y, z)];
-    s32[i] = (k >= lo && k < hi) ? (float)sig[i] : 0.f;
+    s32[t * px + x] = (k >= lo && k < hi) ? (float)sig[i] : 0.f;
   }
 }
 
@@ -376,7 +384,7 @@ k_mixed_residual(Grid g, TileCount tc, CellGrid cg, const int *__restrict__ kx,
                  const double *__restrict__ sig, const double *__restrict__ x64,
                  float *__restrict__ r32, float *__restrict__ p32, short *__restrict__ e16,
                  float *__restrict__ d32, float *__restrict__ xref, MixState *st, double *part,
-                 int nblk_part) {
+                 int nblk_part, int px) {
   using T = Tile<DIM>;
   constexpr int HN = T::HX * T::HY * T::HZ;
   constexpr int TN = T::TX * T::TY * T::TZ;
@@ -447,11 +455,12 @@ k_mixed_residual(Grid g, TileCount tc, CellGrid cg, const int *__restrict__ kx,
         e = ki - (ex - 1);
         acc_add(rho, (double)m * (double)m, -2 * e);
       }
-      r32[gi] = m;
-      p32[gi] = 0.f;
-      e16[gi] = (short)max(-32000, min(e, 32000));
-      d32[gi] = 0.f;
-      xref[gi] = (si != 0.0) ? (float)xi : 0.f;
+      const int64_t pi = gx + (int64_t)px * (gy + (int64_t)g.ny * gz);   // pitched
+      r32[pi] = m;
+      p32[pi] = 0.f;
+      e16[pi] = (short)max(-32000, min(e, 32000));
+      d32[pi] = 0.f;
+      xref[pi] = (si != 0.0) ? (float)xi : 0.f;
     }
     __syncthreads();
   }
@@ -1179,7 +1188,7 @@ k_mixed2d_tma(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ 
               const __grid_constant__ CUtensorMap tm_d, const __grid_constant__ CUtensorMap tm_x,
               Grid g, CellGrid cg, int tiles_x, int ntiles, const int *__restrict__ kx,
               float *__restrict__ r32o, float *__restrict__ p32o, short *__restrict__ e16o,
-              float *__restrict__ d32, MixState *st, double *part, int nblk_part) {
+              float *__restrict__ d32, MixState *st, double *part, int nblk_part, int px) {
   using T = TmaTile<TY>;
   constexpr int RW = TY / RG;   // rows marched by one warp
   static_assert(TY % RG == 0, "rows per warp");
@@ -1262,7 +1271,7 @@ k_mixed2d_tma(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ 
     const int lc = 64 * cw + 2 * lane;          // tile-local column of node 0
     const int x = x0 + lc;
     const int hc = (lane == 0) ? lc - 1 : lc + 2;   // halo column (lanes 0, 31)
-    const float hx0 = (half && x == 0) ? 0.5f : 1.f;
+    const float hx0 = (half && (x == 0 || x == g.nx - 1)) ? 0.5f : 1.f;   // odd nx: x = nx-1
     const float hx1 = (half && x + 1 == g.nx - 1) ? 0.5f : 1.f;
     TRow A, C, B;
     const int j0 = rg * RW + 1;                 // smem row of the first centre row
@@ -1338,7 +1347,7 @@ k_mixed2d_tma(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ 
               if (!(mx <= 3.4e38f)) rmax = INFINITY;
             }
           }
-          const int64_t o = (int64_t)y * g.nx + x;
+          const int64_t o = (int64_t)y * px + x;   // pitched row
           *reinterpret_cast<float2 *>(d32 + o) = make_float2(d[0], d[1]);
           *reinterpret_cast<float2 *>(r32o + o) = make_float2(rn[0], rn[1]);
           *reinterpret_cast<float2 *>(p32o + o) = make_float2(pn[0], pn[1]);
@@ -1424,7 +1433,7 @@ k_mixed3d_tma(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ 
               Grid g, CellGrid cg, int tiles_x, int tiles_y, int zc, int ntiles,
               const int *__restrict__ kx, float *__restrict__ r32o, float *__restrict__ p32o,
               short *__restrict__ e16o, float *__restrict__ d32, MixState *st, double *part,
-              int nblk_part) {
+              int nblk_part, int px) {
   using T = TmaTile<TY>;
   constexpr int NS = kTma3Stages;
   static_assert(NS >= 4, "the plane ring needs four stages (two read, two ahead)");
@@ -1510,7 +1519,7 @@ k_mixed3d_tma(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ 
     const int q0 = k * PL;
     int kcz = -1, kyi = 0;   // cell exponent of (x, y, z), cached per cell in z
     const float wyz = (half && (y == 0 || y == g.ny - 1)) ? 0.5f : 1.f;   // hy
-    const float hx0 = (half && x == 0) ? 0.5f : 1.f;
+    const float hx0 = (half && (x == 0 || x == g.nx - 1)) ? 0.5f : 1.f;   // odd nx: x = nx-1
     const float hx1 = (half && x + 1 == g.nx - 1) ? 0.5f : 1.f;
     // prologue: rows at z0 - 1 (u, exponents) and z0 (full)
     bool ok = wait(q0);
@@ -1610,7 +1619,7 @@ k_mixed3d_tma(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ 
               if (!(mx <= 3.4e38f)) rmax = INFINITY;
             }
           }
-          const int64_t o = ((int64_t)z * g.ny + y) * g.nx + x;
+          const int64_t o = ((int64_t)z * g.ny + y) * px + x;   // pitched rows
           *reinterpret_cast<float2 *>(d32 + o) = make_float2(d[0], d[1]);
           *reinterpret_cast<float2 *>(r32o + o) = make_float2(rn[0], rn[1]);
           *reinterpret_cast<float2 *>(p32o + o) = make_float2(pn[0], pn[1]);
@@ -1638,11 +1647,11 @@ k_mixed3d_tma(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ 
 }
 
 // x64 += d (kx units, unknowns only: d is zero on the sources).
-__global__ void k_mixed_update(int64_t n, const float *__restrict__ d32,
+__global__ void k_mixed_update(int64_t n, int nx, int px, const float *__restrict__ d32,
                                double *__restrict__ x64) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const float d = d32[i];
+    const float d = d32[pidx(i, nx, px)];
     if (d != 0.f) x64[i] += (double)d;
   }
 }
@@ -1693,6 +1702,7 @@ struct MixedState {
   int tma = 0;                   // TMA-staged 2D kernels: variant index (0 = off)
   int tma_tiles_x = 0, tma_ntiles = 0, tma_nblk1 = 0, tma_nblk2 = 0;
   int tma_tiles_y = 0, tma_zc = 0;   // 3D: rows per tile come from the variant
+  int px = 0;                        // row pitch of the FP32 / int16 arrays
   CUtensorMap tm_r[2], tm_p[2], tm_e[2], tm_s, tm_d, tm_x;
   float *s32 = nullptr, *fb = nullptr, *St = nullptr, *d32 = nullptr, *xref = nullptr;
   float *r32[2] = {nullptr, nullptr}, *p32[2] = {nullptr, nullptr};
@@ -1861,14 +1871,14 @@ static EncodeTiledFn encode_fn() {
 
 // Tiled tensor map over a row-major nx x ny (x nz) array, box bw x bh (x 1)
 // elements; nz == 0 gives a 2D map.
-static bool encode_map(CUtensorMap *map, void *base, bool is_short, int nx, int ny, int nz,
-                       int bw, int bh) {
+static bool encode_map(CUtensorMap *map, void *base, bool is_short, int nx, int px, int ny,
+                       int nz, int bw, int bh) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   const size_t es = is_short ? 2 : 4;
   const cuuint32_t rank = nz > 0 ? 3 : 2;
   const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)(nz > 0 ? nz : 1)};
-  const cuuint64_t strides[2] = {(cuuint64_t)nx * es, (cuuint64_t)nx * ny * es};
+  const cuuint64_t strides[2] = {(cuuint64_t)px * es, (cuuint64_t)px * ny * es};
   const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   return fn(map, is_short ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
@@ -1879,17 +1889,17 @@ static bool encode_map(CUtensorMap *map, void *base, bool is_short, int nx, int 
 
 static bool tma_encode(MixedState *m) {
   const int ty = kTmaTYs[m->tma - 1];
-  const int nx = m->g.nx, ny = m->g.ny, nz = (m->g.ndim == 3) ? m->g.nz : 0;
+  const int nx = m->g.nx, px = m->px, ny = m->g.ny, nz = (m->g.ndim == 3) ? m->g.nz : 0;
   const int fw = kTmaTX + 8, ew = kTmaTX + 16, h = ty + 2;
   bool ok = true;
   for (int k = 0; k < 2; ++k) {
-    ok = ok && encode_map(&m->tm_r[k], m->r32[k], false, nx, ny, nz, fw, h);
-    ok = ok && encode_map(&m->tm_p[k], m->p32[k], false, nx, ny, nz, fw, h);
-    ok = ok && encode_map(&m->tm_e[k], m->e16[k], true, nx, ny, nz, ew, h);
+    ok = ok && encode_map(&m->tm_r[k], m->r32[k], false, nx, px, ny, nz, fw, h);
+    ok = ok && encode_map(&m->tm_p[k], m->p32[k], false, nx, px, ny, nz, fw, h);
+    ok = ok && encode_map(&m->tm_e[k], m->e16[k], true, nx, px, ny, nz, ew, h);
   }
-  ok = ok && encode_map(&m->tm_s, m->s32, false, nx, ny, nz, fw, h);
-  ok = ok && encode_map(&m->tm_d, m->d32, false, nx, ny, nz, kTmaTX, ty);
-  ok = ok && encode_map(&m->tm_x, m->xref, false, nx, ny, nz, kTmaTX, ty);
+  ok = ok && encode_map(&m->tm_s, m->s32, false, nx, px, ny, nz, fw, h);
+  ok = ok && encode_map(&m->tm_d, m->d32, false, nx, px, ny, nz, kTmaTX, ty);
+  ok = ok && encode_map(&m->tm_x, m->xref, false, nx, px, ny, nz, kTmaTX, ty);
   return ok;
 }
 
@@ -1931,10 +1941,18 @@ eik_status mixed_create(MixedState **out, const Grid &g, const TileCount &tc, in
   // rows with 4 / 2 columns per lane, 4..7 TMA-staged tiles (variants 1..4
   // listed at kTmaTYs)
   const int vec = (tile_override == 2) ? 4 : 2;
-  const bool tma_ok = g.ndim == 2 && g.nx % 8 == 0 &&
-                      (tile_override == 0 || (tile_override >= 4 && tile_override <= 7) ||
+  // Library choice: TMA tiles where the row pitch is already a multiple of 8
+  // or the grid is large (>= 2^20 nodes; its FP32 arrays are then padded);
+  // small odd-width grids measured faster on the register-marched or generic
+  // kernels (few tiles per block leave the TMA pipeline no depth).  An
+  // explicit TMA variant always pads.
+  const bool tma_default = g.nx % 8 == 0 || g.n >= (int64_t(1) << 20);
+  const bool tma_ok = g.ndim == 2 &&
+                      ((tile_override == 0 && tma_default) ||
+                       (tile_override >= 4 && tile_override <= 7) ||
                        (tile_override >= 10 && tile_override <= 12));
-  const bool tma3_ok = g.ndim == 3 && g.nx % 8 == 0 && (tile_override == 0 || tile_override == 8 || tile_override == 9);
+  const bool tma3_ok = g.ndim == 3 && ((tile_override == 0 && tma_default) ||
+                                       tile_override == 8 || tile_override == 9);
   const bool march_ok = g.ndim == 2 && g.nx % vec == 0 &&
                         (tile_override == 0 || tile_override == 2 || tile_override == 3);
   if (march_ok) {
@@ -1969,10 +1987,15 @@ eik_status mixed_create(MixedState **out, const Grid &g, const TileCount &tc, in
   }
   m->nblk_part = std::max(std::max(m->nblk_stencil, m->cap), m->nblk2d);
   m->nblk_part = std::max(m->nblk_part, std::max(m->tma_nblk1, m->tma_nblk2));
+  // row pitch of the FP32 / int16 arrays: a multiple of 8 for the TMA
+  // kernels (16-byte aligned rows for the tensor maps), nx otherwise
+  m->px = m->tma ? (g.nx + 7) / 8 * 8 : g.nx;
   const int64_t n = g.n;
-  bool ok = mal(&m->s32, n) && mal(&m->d32, n) && mal(&m->xref, n) && mal(&m->r32[0], n) && mal(&m->r32[1], n) &&
-            mal(&m->p32[0], n) && mal(&m->p32[1], n) && mal(&m->e16[0], n) &&
-            mal(&m->e16[1], n) && mal(&m->x64, n) && mal(&m->fb, m->cg.ncell) &&
+  const int64_t np = (g.n / g.nx) * m->px;
+  bool ok = mal(&m->s32, np) && mal(&m->d32, np) && mal(&m->xref, np) && mal(&m->r32[0], np) &&
+            mal(&m->r32[1], np) && mal(&m->p32[0], np) && mal(&m->p32[1], np) &&
+            mal(&m->e16[0], np) && mal(&m->e16[1], np) && mal(&m->x64, n) &&
+            mal(&m->fb, m->cg.ncell) &&
             mal(&m->St, m->cg.ncell) && mal(&m->kx, m->cg.ncell) &&
             mal(&m->part, 8 * (size_t)m->nblk_part) && mal(&m->st, 1);
   if (ok) ok = cudaMallocHost((void **)&m->h_st, sizeof(MixState)) == cudaSuccess;
@@ -2019,11 +2042,11 @@ static void launch_residual(MixedState *m, const MixedArgs &a) {
   if (m->g.ndim == 2)
     k_mixed_residual<2><<<m->nblk_stencil, kThreads, 0, a.stream>>>(
         m->g, m->tc, m->cg, m->kx, a.sig, m->x64, m->r32[0], m->p32[0], m->e16[0], m->d32,
-        m->xref, m->st, m->part, m->nblk_part);
+        m->xref, m->st, m->part, m->nblk_part, m->px);
   else
     k_mixed_residual<3><<<m->nblk_stencil, kThreads, 0, a.stream>>>(
         m->g, m->tc, m->cg, m->kx, a.sig, m->x64, m->r32[0], m->p32[0], m->e16[0], m->d32,
-        m->xref, m->st, m->part, m->nblk_part);
+        m->xref, m->st, m->part, m->nblk_part, m->px);
   m->launches[2]++;
 }
 
@@ -2039,13 +2062,13 @@ static void launch_iteration(MixedState *m, int set, cudaStream_t s, bool timed 
         <<<m->tma_nblk1, 64 * RG, TmaTile<TY>::smem(false, NS), s>>>(                           \
         m->tm_r[a], m->tm_p[a], m->tm_e[a], m->tm_s, m->tm_d, m->tm_x, m->g, m->cg,             \
         m->tma_tiles_x, m->tma_ntiles, m->kx, nullptr, nullptr, nullptr, m->d32, m->st, p1,     \
-        m->nblk_part);                                                                          \
+        m->nblk_part, m->px);                                                                   \
     if (timed) cudaEventRecord(m->ev[1], s);                                                    \
     k_mixed2d_tma<true, TY, RG, NS>                                                             \
         <<<m->tma_nblk2, 64 * RG, TmaTile<TY>::smem(true, NS), s>>>(                            \
         m->tm_r[a], m->tm_p[a], m->tm_e[a], m->tm_s, m->tm_d, m->tm_x, m->g, m->cg,             \
         m->tma_tiles_x, m->tma_ntiles, m->kx, m->r32[b], m->p32[b], m->e16[b], m->d32, m->st,   \
-        p2, m->nblk_part);                                                                      \
+        p2, m->nblk_part, m->px);                                                               \
     if (timed) cudaEventRecord(m->ev[2], s);                                                    \
   } while (0)
 #define EIK_LAUNCH_TMA3(TY)                                                                     \
@@ -2055,12 +2078,12 @@ static void launch_iteration(MixedState *m, int set, cudaStream_t s, bool timed 
     k_mixed3d_tma<false, TY><<<m->tma_nblk1, 64 * TY, kTma3Stages * T3::STAGE1 + 128, s>>>(     \
         m->tm_r[a], m->tm_p[a], m->tm_e[a], m->tm_s, m->tm_d, m->tm_x, m->g, m->cg,             \
         m->tma_tiles_x, m->tma_tiles_y, m->tma_zc, m->tma_ntiles, m->kx, nullptr, nullptr,      \
-        nullptr, m->d32, m->st, p1, m->nblk_part);                                              \
+        nullptr, m->d32, m->st, p1, m->nblk_part, m->px);                                       \
     if (timed) cudaEventRecord(m->ev[1], s);                                                    \
     k_mixed3d_tma<true, TY><<<m->tma_nblk2, 64 * TY, kTma3Stages * T3::STAGE2 + 128, s>>>(      \
         m->tm_r[a], m->tm_p[a], m->tm_e[a], m->tm_s, m->tm_d, m->tm_x, m->g, m->cg,             \
         m->tma_tiles_x, m->tma_tiles_y, m->tma_zc, m->tma_ntiles, m->kx, m->r32[b], m->p32[b],  \
-        m->e16[b], m->d32, m->st, p2, m->nblk_part);                                            \
+        m->e16[b], m->d32, m->st, p2, m->nblk_part, m->px);                                     \
     if (timed) cudaEventRecord(m->ev[2], s);                                                    \
   } while (0)
     switch (m->tma) {
@@ -2253,7 +2276,7 @@ static eik_status refine(MixedState *m, const MixedArgs &a, int lo, int hi, int 
       result = EIK_ERR_BREAKDOWN;
       break;
     }
-    k_mixed_update<<<blocks(g.n), kThreads, 0, s>>>(g.n, m->d32, m->x64);
+    k_mixed_update<<<blocks(g.n), kThreads, 0, s>>>(g.n, g.nx, m->px, m->d32, m->x64);
     m->launches[5]++;
     MCK(cudaGetLastError());
   }
@@ -2272,7 +2295,7 @@ eik_status mixed_solve(MixedState *m, const MixedArgs &a, int *inner_iters, int 
     return (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, cap));
   };
   // setup: FP32 coefficients, cell means of f, coarse distance -> exponents
-  k_sig32<<<blocks(g.n), kThreads, 0, s>>>(g.n, a.sig, m->s32);
+  k_sig32<<<blocks(g.n), kThreads, 0, s>>>(g.n, g.nx, m->px, a.sig, m->s32);
   k_cell_mean<<<m->cg.ncell, kThreads, 0, s>>>(g, m->cg, a.f, m->fb);
   const size_t smem = 2 * sizeof(float) * m->cg.ncell;
   k_coarse_exponents<<<1, 1024, smem, s>>>(g, m->cg, g.hbar / g.sqrt_c, m->fb, a.src, a.U,
@@ -2313,7 +2336,8 @@ eik_status mixed_solve(MixedState *m, const MixedArgs &a, int *inner_iters, int 
     for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
       for (int lo = kmin;; lo += band_bits) {
         const int hi = std::min(lo + band_bits + ov, kmax + 1);
-        k_sig32_band<<<blocks(g.n), kThreads, 0, s>>>(g, m->cg, m->kx, lo, hi, a.sig, m->s32);
+        k_sig32_band<<<blocks(g.n), kThreads, 0, s>>>(g, m->px, m->cg, m->kx, lo, hi, a.sig,
+                                                      m->s32);
         m->launches[0]++;
         MCK(cudaGetLastError());
         if (trace) fprintf(stderr, "[mixed] sweep %d band [%d, %d)\n", sweep, lo, hi);
@@ -2321,7 +2345,7 @@ eik_status mixed_solve(MixedState *m, const MixedArgs &a, int *inner_iters, int 
         if (bs != EIK_OK && bs != EIK_ERR_NOT_CONVERGED) return bs;   // breakdown, timeout, CUDA
         if (hi > kmax || total >= a.opt.max_iter) break;
       }
-      k_sig32<<<blocks(g.n), kThreads, 0, s>>>(g.n, a.sig, m->s32);
+      k_sig32<<<blocks(g.n), kThreads, 0, s>>>(g.n, g.nx, m->px, a.sig, m->s32);
       m->launches[0]++;
       int checks = 0;
       result = refine(m, a, INT_MIN, INT_MAX, 0, &total, &checks, res_cw, trace);

@@ -185,3 +185,24 @@ def test_kernel_variants_agree_with_oracle(eik, ndim, tile_override):
     eik.eik_destroy(h)
     S_ref, _, _ = fd.solve(inst.f, inst.dims, inst.h, inst.hbar, inst.src_idx)
     assert np.max(np.abs(S.cpu().numpy().ravel() - S_ref)) <= S_ABS
+
+
+@pytest.mark.parametrize("dims,tile_override", [((263, 131), 6), ((263, 131), 10),
+                                                ((41, 23, 19), 8), ((41, 23, 19), 9)])
+def test_tma_kernels_on_odd_widths(eik, dims, tile_override):
+    """The TMA kernels on grids whose width is not a multiple of 8: the FP32
+    arrays get a padded row pitch (and the last node of a row can be the
+    first of a lane's pair)."""
+    import torch
+    rng = np.random.default_rng(sum(dims))
+    h = 1.0 / (max(dims) - 1)
+    f = wl.fourier_field(rng, dims, h)
+    src = wl.random_sources(rng, int(np.prod(dims)), 3)
+    inst = wl.Instance(dims, h, 4 * h, f, src, np.zeros(len(src)))
+    opt = eik.make_options(precision="mixed", tol=1e-9, tile_override=tile_override)
+    hd = eik.eik_create(inst.dims, inst.h, inst.hbar, torch.from_numpy(inst.f).cuda(),
+                        inst.src_idx, None, opt)
+    S, _, _ = eik.eik_solve(hd)
+    eik.eik_destroy(hd)
+    S_ref, _, _ = fd.solve(inst.f, inst.dims, inst.h, inst.hbar, inst.src_idx)
+    assert np.max(np.abs(S.cpu().numpy().ravel() - S_ref)) <= S_ABS
