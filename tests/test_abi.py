@@ -89,3 +89,32 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert st == _lib.EIK_ERR_ARG
     assert "ndim" in _lib.last_error()
     assert lib.eik_destroy(None) == _lib.EIK_OK
+
+
+def test_path_and_forcing_entry_points_validate_arguments_without_gpu(lib):
+    """Argument checks of the path-planning, forcing and allocation-free
+    entry points run before any CUDA call."""
+    from paper_1403_1937_gb300 import _lib
+    d1 = (ctypes.c_int64 * 1)(63)
+    d2 = (ctypes.c_int64 * 2)(9, 7)
+    dbad = (ctypes.c_int64 * 2)(1, 7)
+    P = ctypes.c_void_p(0x1000)      # never dereferenced: the checks fail first
+    assert lib.eik_grad_S(1, d1, 0.1, P, P, None) == _lib.EIK_ERR_ARG       # ndim
+    assert lib.eik_grad_S(2, dbad, 0.1, P, P, None) == _lib.EIK_ERR_ARG     # size < 2
+    assert lib.eik_grad_S(2, d2, 0.0, P, P, None) == _lib.EIK_ERR_ARG       # h <= 0
+    assert lib.eik_grad_S(2, d2, 0.1, None, P, None) == _lib.EIK_ERR_ARG    # null S
+    # step <= 0, eps < 0, max_steps < 0, npaths < 0
+    for step, eps, ms, npaths in ((0.0, 0.1, 5, 1), (0.1, -1.0, 5, 1), (0.1, 0.1, -1, 1),
+                                  (0.1, 0.1, 5, -1)):
+        assert lib.eik_backtrack(2, d2, 0.1, P, P, npaths, step, ms, P, 1, eps, P, P, P,
+                                 None) == _lib.EIK_ERR_ARG
+    assert lib.eik_backtrack(2, d2, 0.1, P, P, 0, 0.1, 5, P, 1, 0.1, P, P, P,
+                             None) == _lib.EIK_OK                           # nothing to do
+    assert lib.eik_sfs_forcing(P, -1, 0.0, P, None) == _lib.EIK_ERR_ARG
+    assert lib.eik_sfs_forcing(P, 4, -0.1, P, None) == _lib.EIK_ERR_ARG
+    assert lib.eik_sfs_forcing(None, 4, 0.0, P, None) == _lib.EIK_ERR_ARG
+    assert lib.eik_sfs_forcing(None, 0, 0.0, None, None) == _lib.EIK_OK
+    big = (ctypes.c_int64 * 2)(1025, 1024)                                  # > 2^20 nodes
+    res = ctypes.c_void_p(0x1000)
+    assert lib.eik_residual_noalloc(2, big, 0.1, 0.1, P, P, P, 1, 0, res, None) == \
+        _lib.EIK_ERR_ARG
