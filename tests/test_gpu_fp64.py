@@ -93,6 +93,7 @@ def test_random_ragged(eik, seed, ndim, boundary, with_U):
     ((33, 2, 2), [0, 33, 66, 99]),          # 3D slab
     ((64, 32), [5, 5, 5]),                  # exact tile size, duplicate source
     ((65, 33), [64 + 65 * 32]),             # one past the tile, far corner source
+    ((3, 2), [0, 1, 2, 3, 4, 5]),           # every node a source: no unknowns
 ])
 def test_edge_cases(eik, dims, src):
     n = int(np.prod(dims))

@@ -206,3 +206,28 @@ def test_tma_kernels_on_odd_widths(eik, dims, tile_override):
     eik.eik_destroy(hd)
     S_ref, _, _ = fd.solve(inst.f, inst.dims, inst.h, inst.hbar, inst.src_idx)
     assert np.max(np.abs(S.cpu().numpy().ravel() - S_ref)) <= S_ABS
+
+
+@pytest.mark.parametrize("dims,src", [
+    ((2, 2), [0, 1, 2]),                    # one unknown
+    ((3, 3), [0, 2, 6, 8]),                 # corners
+    ((5, 4), [7, 8]),                       # adjacent sources
+    ((65, 2), list(range(0, 130, 65))),     # slab, x = 0 face
+    ((2, 2, 2), [7]),
+    ((33, 2, 2), [0, 33, 66, 99]),          # 3D slab
+    ((128, 16), [5, 5, 5]),                 # exactly one TMA tile, duplicate source
+    ((129, 17), [128 + 129 * 16]),          # one past the tile, far corner source
+    ((3, 2), [0, 1, 2, 3, 4, 5]),           # every node a source: no unknowns
+])
+def test_edge_cases_mixed(eik, dims, src):
+    n = int(np.prod(dims))
+    inst = wl.Instance(dims, 1.0 / (max(dims) - 1), 0.3 / (max(dims) - 1) * 4,
+                       np.random.default_rng(n).uniform(0.5, 2.0, dims[::-1]),
+                       np.array(src, dtype=np.int64), np.zeros(len(src)))
+    S, _, stats, _ = mixed_solve(eik, inst)
+    if len(set(src)) == n:
+        assert np.all(S == 0.0)
+        return
+    S_ref, _, sys = fd.solve(inst.f, inst.dims, inst.h, inst.hbar, inst.src_idx)
+    assert np.max(np.abs(S - S_ref)) <= S_ABS
+    assert np.array_equal(S[sys.src], sys.U)
