@@ -117,8 +117,9 @@ typedef struct {
   int band_bits;      /* mixed mode: when the coarse distance estimate puts
                          phi over more than 2 * band_bits powers of two, the
                          solve sweeps level-set bands of band_bits powers of
-                         two (nearest first, half a band of overlap), holding
-                         the rest as Dirichlet data; 0 = library choice (48),
+                         two (nearest first, an overlap of at least 32),
+                         holding the rest as Dirichlet data; 0 = library
+                         choice (bands of 40 when the range exceeds 96),
                          negative = never sweep */
   int test_flags;     /* test hook, 0 in normal use.  Bit 0 (mixed mode, 2D
                          TMA kernels): one block of the inner CG's first

@@ -57,7 +57,11 @@ namespace {
 constexpr int kInnerGraphIters = 32;   // even: the buffer sets alternate
 constexpr int kNoExp = 30000;          // exponent of an all-zero node
 constexpr int kMaxCells = 16384;
-constexpr int kBandBits = 48;          // level-set band width (powers of two of phi)
+// level-set sweep (library choice): bands of kBandBits powers of two of phi,
+// used when kx spans more than kSweepBits (measured on 2048^2: 40-bit bands
+// took 2696 inner iterations, 48-bit ones 2845, 32-bit ones 3074)
+constexpr int kBandBits = 40;
+constexpr int kSweepBits = 96;
 constexpr int kMaxSweeps = 4;
 // first inner solve of a refinement step: reduce the kx-scaled max-norm
 // residual by this factor (measured on the 2048^2 and 256^3 workloads:
@@ -2321,7 +2325,8 @@ eik_status mixed_solve(MixedState *m, const MixedArgs &a, int *inner_iters, int 
   const int max_outer = (a.opt.max_outer > 0) ? a.opt.max_outer : 30;
   int total = 0, outer = 0;
   eik_status result;
-  if (a.opt.band_bits < 0 || kmax - kmin <= 2 * band_bits) {
+  const int sweep_bits = (a.opt.band_bits > 0) ? 2 * a.opt.band_bits : kSweepBits;
+  if (a.opt.band_bits < 0 || kmax - kmin <= sweep_bits) {
     result = refine(m, a, INT_MIN, INT_MAX, max_outer, &total, &outer, res_cw, trace);
   } else {
     // Level-set sweep: bands of band_bits powers of two in kx (plus an outer
