@@ -94,18 +94,37 @@ __global__ void k_rho_max(int64_t n, double *__restrict__ sc, double *out) {
   __shared__ double red[32];
   __shared__ int flag;
   double m = 0.0;
+  bool nan_seen = false;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double v = sc[kRhoOff + i];
-    m = (v > m || v != v) ? v : m;   // keeps a NaN
+    if (v != v)
+      nan_seen = true;   // fmax in the reductions below would drop it
+    else
+      m = fmax(m, v);
   }
+  // A NaN residual (NaN in S, or inf - inf between two +inf neighbours) must
+  // not come back as a small finite maximum: the block's partial becomes NaN
+  // and the last block turns the result into NaN.  The partial travels
+  // through the same fence and ticket as the maxima.
+  nan_seen = __syncthreads_or(nan_seen) != 0;
   m = eik::block_max(m, red);
-  if (threadIdx.x == 0) sc[kPartOff + blockIdx.x] = m;
+  if (threadIdx.x == 0) sc[kPartOff + blockIdx.x] = nan_seen ? NAN : m;
   unsigned int *ticket = reinterpret_cast<unsigned int *>(sc + kFlagOff);
   if (!eik::last_block(ticket, &flag)) return;
-  const double tot = eik::max_partials(sc + kPartOff, gridDim.x, red);
+  double tot = 0.0;
+  bool any_nan = false;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    const double v = __ldcg(sc + kPartOff + b);
+    if (v != v)
+      any_nan = true;
+    else
+      tot = fmax(tot, v);
+  }
+  any_nan = __syncthreads_or(any_nan) != 0;
+  tot = eik::block_max(tot, red);
   if (threadIdx.x == 0) {
-    *out = (sc[kFlagOff + 1] != 0.0) ? NAN : tot;
+    *out = (any_nan || sc[kFlagOff + 1] != 0.0) ? NAN : tot;
     *ticket = 0u;
   }
 }
@@ -118,12 +137,14 @@ extern "C" eik_status eik_residual_noalloc(int ndim, const int64_t *dims, double
                                            double *res_max, eik_stream_t stream) {
   if (ndim != 2 && ndim != 3) return EIK_ERR_ARG;
   if (!dims || !f || !S || !res_max || (nsrc > 0 && !src_idx)) return EIK_ERR_ARG;
-  if (!(h > 0) || !(hbar > 0)) return EIK_ERR_ARG;
+  if (!(h > 0) || !(hbar > 0) || !isfinite(h) || !isfinite(hbar)) return EIK_ERR_ARG;
   if (boundary != EIK_BOUNDARY_HALF_CELL && boundary != EIK_BOUNDARY_DROP_EDGE) return EIK_ERR_ARG;
   int64_t d[3] = {1, 1, 1}, n = 1;
   for (int a = 0; a < ndim; ++a) {
     d[a] = dims[a];
-    if (d[a] < 2) return EIK_ERR_ARG;
+    // each extent is bounded before it is multiplied in, so the product
+    // cannot wrap around (and every extent fits an int)
+    if (d[a] < 2 || d[a] > kNoAllocMaxNodes) return EIK_ERR_ARG;
     n *= d[a];
     if (n > kNoAllocMaxNodes) return EIK_ERR_ARG;   // larger than the scratch array
   }

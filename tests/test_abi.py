@@ -118,3 +118,13 @@ def test_path_and_forcing_entry_points_validate_arguments_without_gpu(lib):
     res = ctypes.c_void_p(0x1000)
     assert lib.eik_residual_noalloc(2, big, 0.1, 0.1, P, P, P, 1, 0, res, None) == \
         _lib.EIK_ERR_ARG
+    # extents whose product wraps around int64 to a small number (3 * 6148914691236517206
+    # = 2 mod 2^64) are rejected before they are multiplied
+    wrap = (ctypes.c_int64 * 2)(3, 6148914691236517206)
+    assert lib.eik_residual_noalloc(2, wrap, 0.1, 0.1, P, P, P, 1, 0, res, None) == \
+        _lib.EIK_ERR_ARG
+    ok = (ctypes.c_int64 * 2)(9, 7)
+    for hh, hb in ((float("inf"), 0.1), (0.1, float("inf")), (float("nan"), 0.1),
+                   (0.1, float("nan")), (-0.1, 0.1), (0.1, 0.0)):
+        assert lib.eik_residual_noalloc(2, ok, hh, hb, P, P, P, 1, 0, res, None) == \
+            _lib.EIK_ERR_ARG, (hh, hb)

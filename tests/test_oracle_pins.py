@@ -364,3 +364,138 @@ def test_cg_oracle_max_iter_reports_not_converged():
     _, _, _, info = cg.solve(inst.f, inst.dims, inst.h, inst.hbar,
                              inst.src_idx, tol=1e-13, max_iter=20)
     assert info["status"] == 1 and info["iters"] == 20
+
+
+# ------------------------------------------- relative-form (underflow) solve
+# fd.solve_relative is the oracle for every problem whose phi underflows
+# float64 (S/hbar > ~700).  It rests on fd.graph_distance for its scale.  The
+# pins below tie both to facts outside them: closed-form grid distances, a
+# brute-force shortest path, the direct solve where both work, the exact
+# slab solution beyond the float64 range, and the lattice Green's function.
+
+def _octile(d):
+    """Shortest path length on the 8- (2D) / 26- (3D) neighbour lattice with
+    unit spacing: straight moves, face diagonals and (3D) body diagonals."""
+    a = sorted((abs(v) for v in d), reverse=True) + [0, 0]
+    return (a[0] - a[1]) + np.sqrt(2.0) * (a[1] - a[2]) + np.sqrt(3.0) * a[2]
+
+
+@pytest.mark.parametrize("dims,srcs,U", [
+    ((9, 7), [(2, 3)], [0.0]),
+    ((11, 6), [(0, 0), (10, 5)], [0.0, 0.3]),
+    ((5, 6, 4), [(1, 4, 2)], [0.0]),
+    ((6, 5, 7), [(0, 0, 0), (5, 4, 6)], [0.2, 0.0]),
+])
+def test_graph_distance_uniform_is_lattice_metric(dims, srcs, U):
+    """Constant f: the graph distance is f h times the lattice (octile)
+    metric, minimised over the sources with the offsets U_k - U_min."""
+    h, f0 = 0.1, 1.7
+    F = np.full(dims[::-1], f0)
+    sys = fd.assemble(F, dims, h, 0.05, [wl.flat_index(dims, s) for s in srcs], U)
+    d = fd.graph_distance(sys)
+    coords = np.stack(np.unravel_index(np.arange(sys.n), dims[::-1])[::-1], -1)
+    Umin = min(U)
+    want = np.full(sys.n, np.inf)
+    for s, u in zip(srcs, U):
+        dd = np.array([_octile(c - np.array(s)) for c in coords])
+        want = np.minimum(want, (u - Umin) + f0 * h * dd)
+    assert np.max(np.abs(d - want)) < 1e-12
+
+
+def test_graph_distance_brute_force_bellman_ford():
+    """Random f on a small grid: pure-Python Bellman-Ford over the same
+    neighbour set and edge cost (length x mean of f at the two ends)."""
+    rng = np.random.default_rng(5)
+    for dims in [(5, 4), (3, 4, 3)]:
+        n = int(np.prod(dims))
+        F = rng.uniform(0.5, 2.0, size=dims[::-1])
+        h = 0.3
+        src = [0, n - 2]
+        U = [0.1, 0.0]
+        sys = fd.assemble(F, dims, h, 0.05, src, U)
+        d = fd.graph_distance(sys)
+        fl = F.ravel()
+        coords = [tuple(int(v) for v in np.unravel_index(i, dims[::-1])[::-1]) for i in range(n)]
+        index = {c: i for i, c in enumerate(coords)}
+        dist = [np.inf] * n
+        dist[src[0]] = U[0] - min(U)
+        dist[src[1]] = U[1] - min(U)
+        import itertools
+        offs = [o for o in itertools.product((-1, 0, 1), repeat=len(dims)) if any(o)]
+        for _ in range(n):
+            for i, c in enumerate(coords):
+                for o in offs:
+                    j = index.get(tuple(a + b for a, b in zip(c, o)))
+                    if j is None:
+                        continue
+                    cost = h * np.sqrt(sum(v * v for v in o)) * 0.5 * (fl[i] + fl[j])
+                    if dist[j] + cost < dist[i]:
+                        dist[i] = dist[j] + cost
+        assert np.max(np.abs(d - np.array(dist))) < 1e-12
+
+
+@pytest.mark.parametrize("seed,ndim,boundary,with_U", [
+    (0, 2, 0, False), (1, 2, 1, True), (2, 3, 0, True), (3, 3, 1, False),
+    (4, 2, 0, True),
+])
+def test_solve_relative_equals_direct(seed, ndim, boundary, with_U):
+    """Where phi is representable, the relative-form solve (diagonal
+    similarity D^-1 A D) gives the direct solution, for the graph-distance
+    scale and for arbitrary other scales: the result must not depend on D."""
+    inst = wl.random_small(400 + seed, ndim=ndim, max_side=18 if ndim == 2 else 8,
+                           nsrc_max=3, with_U=with_U)
+    S, _, sys = fd.solve(inst.f, inst.dims, inst.h, inst.hbar, inst.src_idx,
+                         inst.src_U, boundary)
+    rng = np.random.default_rng(seed)
+    gd = fd.graph_distance(sys)
+    scales = [None, np.zeros(sys.n), 0.7 * gd + inst.hbar * rng.uniform(-5, 5, sys.n),
+              rng.uniform(0.0, 40 * inst.hbar, sys.n)]
+    for sc in scales:
+        Sr = fd.solve_relative(sys, sc)
+        assert np.array_equal(Sr[sys.src], sys.U)
+        assert np.max(np.abs(Sr - S)) < 1e-11 * max(1.0, np.abs(S).max())
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_solve_relative_slab_beyond_float64(axis):
+    """Sources filling one face, constant f, S/hbar up to ~830 at the far
+    face: phi = exp(-S/hbar) underflows float64 there, so the direct solve
+    fails, while the relative solve matches the exact slab solution
+    (discrete analogue of Eq. GreensFunction1D) to rounding."""
+    n, f0 = 600, 1.0
+    h = 1.0 / (n - 1)
+    hbar = h / 1.5                      # kappa = arccosh(2.125) = ln 4
+    ndim = 3 if axis == 2 else 2
+    dims = [2] * ndim
+    dims[axis] = n
+    dims = tuple(dims)
+    F = np.full(dims[::-1], f0)
+    src = [k for k in range(int(np.prod(dims)))
+           if np.unravel_index(k, dims[::-1])[::-1][axis] == 0]
+    ex = closed_forms.slab_S(n, f0, h, hbar)
+    assert ex.max() / hbar > 800
+    sys = fd.assemble(F, dims, h, hbar, src)
+    Sr = fd.solve_relative(sys)
+    Sg = np.moveaxis(Sr.reshape(dims[::-1]), ndim - 1 - axis, -1)
+    assert np.max(np.abs(Sg - ex)) < 1e-12 * ex.max()
+    with np.errstate(all="ignore"):
+        Sd, _, _ = fd.solve(F, dims, h, hbar, src)
+    Sdg = np.moveaxis(Sd.reshape(dims[::-1]), ndim - 1 - axis, -1)
+    assert not np.all(np.abs(Sdg - ex) < 1e-6)      # the direct solve cannot
+    # a second, unrelated scale gives the same answer beyond float64 too
+    Sr2 = fd.solve_relative(sys, fd.graph_distance(sys) * 0.9 + 3 * hbar)
+    assert np.max(np.abs(Sr2 - Sr)) < 1e-12 * ex.max()
+
+
+@pytest.mark.parametrize("dims,h,hbar,src", [
+    ((17, 13), 1 / 16, 0.05, (5, 4)),
+    ((9, 9, 9), 1 / 8, 0.1, (4, 4, 4)),
+    ((21, 8), 1 / 20, 0.02, (20, 7)),
+])
+def test_solve_relative_lattice_green_log_form(dims, h, hbar, src):
+    """Single source, constant f: S of the relative solve equals
+    -hbar log of the image sum of the lattice Green's function."""
+    ph = closed_forms.image_phi(dims, h, hbar, 1.0, src)
+    sys = fd.assemble(np.ones(dims[::-1]), dims, h, hbar, [wl.flat_index(dims, src)])
+    Sr = fd.solve_relative(sys).reshape(dims[::-1])
+    assert np.max(np.abs(Sr - (-hbar * np.log(ph)))) < 1e-12 * max(1.0, Sr.max())
