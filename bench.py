@@ -39,8 +39,11 @@ UNIT = "GLUPS"
 ALGO_BYTES_PER_NODE = {
     "cg_pass1_64": 32,   # read r, p, sig; write q            (4 x 8 B)
     "cg_pass2_64": 56,   # read x, r, p, q; write x, r, p     (7 x 8 B)
-    "mixed_pass1": 14,   # read r, p (f32), e (i16), sig (f32)
-    "mixed_pass2": 32,   # read r, p, e, sig, d; write r, p, e (other set), d
+    # one single-reduction FP32 inner iteration: read r, p, sig, d; write r,
+    # p (other buffer set) and d (7 x 4 B); the checking passes (every 4th
+    # in later refinement steps) also read the FP32 iterate, not counted
+    "mixed_cg": 28,
+    "mixed_cg_init": 8,  # first pass of an inner solve: read r, sig
 }
 
 # The FP64 passes are bound by the FP64 pipe, not by HBM: their roofline is
@@ -78,8 +81,8 @@ def parse():
                     help="mixed mode level-set band width (eik_options.band_bits): "
                          "0 library choice, negative never sweep")
     ap.add_argument("--tile-override", type=int, default=0,
-                    help="kernel variant (eik_options.tile_override): 0 library choice, "
-                         "1 generic halo tiles, 2 four columns per lane in 2D")
+                    help="inner-CG kernel variant (eik_options.tile_override): 0 library "
+                         "choice, 1..4 the variants listed in include/eik.h")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=0,

@@ -90,25 +90,13 @@ typedef struct {
   int boundary;       /* EIK_BOUNDARY_*; default half cell */
   int tile_override;  /* mixed-mode inner-CG kernel variant (results agree
                          to rounding; for tuning and tests):
-                         0 = library choice: TMA-staged tiles of 128 x 16
-                             nodes in 2D, 128 x 4 rows marching in z in 3D,
-                             when nx % 8 == 0 or the grid has >= 2^20 nodes
-                             (the FP32 arrays then get a row pitch rounded up
-                             to 8 for the tensor maps); otherwise warp-marched
-                             rows (2D, even nx) or generic kernels;
-                         1 = generic halo-tile kernels everywhere;
-                         2 / 3 = warp-marched rows, 4 / 2 columns per lane
-                             (2D, nx divisible by that);
-                         4..7 = TMA-staged tiles (2D) with
-                             (rows per tile, warps per block) = (16, 4),
-                             (32, 8), (16, 8), (32, 4);
-                         8 / 9 = TMA-staged z-marching tiles (3D) of
-                             4 / 8 rows (3D default: 4);
-                         10..12 = TMA-staged tiles (2D) with
-                             (rows, warps, pipeline stages) = (8, 8, 4),
-                             (16, 8, 3), (8, 4, 4).
-                         A variant whose condition fails falls back to the
-                         generic kernels. */
+                         0 = library choice (variant 1);
+                         2D (every warp an independent pipeline over tiles
+                         of 128 columns): 1..4 = (warps per block, row
+                         stages per warp) = (8, 8), (8, 6), (4, 8), (4, 12);
+                         3D (a block marches 128 x TY rows through z):
+                         1..4 = (TY, plane stages) = (8, 4), (12, 4), (4, 4),
+                         (8, 3).  Other values return EIK_ERR_ARG. */
   double inner_tol;   /* mixed mode: factor by which the first FP32 inner
                          solve of a refinement step reduces the residual
                          (scaled max norm); 0 = library choice (1e-1) */
@@ -121,12 +109,12 @@ typedef struct {
                          holding the rest as Dirichlet data; 0 = library
                          choice (bands of 40 when the range exceeds 96),
                          negative = never sweep */
-  int test_flags;     /* test hook, 0 in normal use.  Bit 0 (mixed mode, 2D
-                         TMA kernels): one block of the inner CG's first
-                         pass never gets its first tile copy, so its bounded
-                         wait (0.2 s) expires and the solve returns
-                         EIK_ERR_TIMEOUT; exercises the timeout path without
-                         any fault. */
+  int test_flags;     /* test hook, 0 in normal use.  Bit 0 (mixed mode): in
+                         the first inner-CG iteration one pipeline (a warp
+                         in 2D, a block in 3D) never gets its first copy,
+                         so its bounded wait (0.2 s) expires and the solve
+                         returns EIK_ERR_TIMEOUT; exercises the timeout path
+                         without any fault. */
   int reserved[5];
 } eik_options;
 
@@ -156,7 +144,7 @@ void eik_default_options(eik_options *opt);
  *   stream   CUDA stream whose work orders the library's work (may be NULL for
  *            the legacy default stream).
  * Allocates device memory proportional to N (about 7 float64 vectors; the
- * mixed mode adds about 5 float32 vectors).  Returns EIK_ERR_OOM if that
+ * mixed mode adds one float64 and 7 float32 vectors).  Returns EIK_ERR_OOM if that
  * fails.
  */
 eik_status eik_create(eik_handle **out, int ndim, const int64_t *dims,

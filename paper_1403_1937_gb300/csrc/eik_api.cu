@@ -423,6 +423,8 @@ eik_status eik_create(eik_handle **out, int ndim, const int64_t *dims, double hs
   if (o.stop_norm != EIK_STOP_COMPONENTWISE && o.stop_norm != EIK_STOP_NORMWISE)
     return fail(EIK_ERR_ARG, "unknown stop_norm");
   if (!(o.tol > 0) || o.max_iter < 1) return fail(EIK_ERR_ARG, "tol and max_iter must be > 0");
+  if (o.tile_override < 0 || o.tile_override > 4)
+    return fail(EIK_ERR_ARG, "tile_override must be in 0..4");
 
   eik_handle *h = new (std::nothrow) eik_handle();
   if (!h) return fail(EIK_ERR_OOM, "host allocation failed");

@@ -25,11 +25,11 @@ def test_roofline_mixed_is_hbm_bound():
     peak, _ = bench.measured_peaks()
     inst = _Inst((2048, 2048))
     # kernel -> (avg ms per timed launch, timed launches, total ms)
-    res = {"kernel_ms": {"mixed_pass1": (0.03, 10, 0.3), "mixed_pass2": (0.04, 10, 0.4),
+    res = {"kernel_ms": {"mixed_cg_init": (0.03, 10, 0.3), "mixed_cg": (0.04, 10, 0.4),
                          "mixed_residual64": (0.4, 1, 0.4)}}
     r = bench.roofline(res, inst, "c2")
-    assert r["bound"] == "hbm" and r["kernel"] == "mixed_pass2" and r["unit"] == "GB/s"
-    algo = 32 * inst.n
+    assert r["bound"] == "hbm" and r["kernel"] == "mixed_cg" and r["unit"] == "GB/s"
+    algo = 28 * inst.n
     assert r["algorithmic_bytes_per_launch"] == algo
     assert r["achieved"] == pytest.approx(algo / 0.04e-3 / 1e9, rel=1e-3)
     assert r["frac"] == pytest.approx(r["achieved"] / peak, abs=2e-4)
@@ -65,7 +65,6 @@ def test_recorded_traffic_matches_the_committed_kernels():
     """Every entry of profiles/traffic.json for the default kernels is keyed
     to the current source, so the bench reports it (not null)."""
     import bench
-    for key in ("mixed_pass1@c2", "mixed_pass2@c2", "mixed_pass1@c3", "mixed_pass2@c3",
-                "cg_pass1_64@c2", "cg_pass2_64@c2"):
+    for key in ("cg_pass1_64@c2", "cg_pass2_64@c2"):
         kernel, wl = key.split("@")
         assert bench.ncu_traffic(kernel, wl) is not None, key

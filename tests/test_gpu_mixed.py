@@ -1,5 +1,5 @@
-"""Mixed-precision path (FP32 block-floating-point inner CG + FP64 iterative
-refinement) vs the CPU oracle, through the C ABI.
+"""Mixed-precision path (FP32 single-reduction inner CG in per-cell exponent
+units + FP64 iterative refinement) vs the CPU oracle, through the C ABI.
 
 Bar: S absolute error <= 1e-6 against the FP64 oracle, on every
 config, including problems whose phi underflows float64 (S/hbar > 700), where
@@ -44,7 +44,7 @@ def test_c1_mixed(eik):
     assert np.max(np.abs(S - S_ref)) <= S_ABS
     assert S[inst.src_idx[0]] == 0.0
     assert stats["res_cw"] <= 1e-9
-    assert kst["mixed_pass1"][0] > 0 and kst["mixed_pass2"][0] > 0
+    assert kst["mixed_cg_init"][0] > 0 and kst["mixed_cg"][0] > 0
     assert kst["cg_pass1_64"][0] == 0      # the FP64 CG did not run
 
 
@@ -148,8 +148,8 @@ def test_band_width_does_not_change_the_solution(eik, band_bits):
 
 
 def test_bounded_wait_timeout_is_reported(eik):
-    """Failure detection without a fault: with test_flags bit 0 one block of
-    the first TMA pass never gets its tile copy; its bounded wait expires,
+    """Failure detection without a fault: with test_flags bit 0 one warp of
+    the first inner iteration never gets its row copy; its bounded wait expires,
     the kernel sets the fault flag, waits (bounded) for its own copies in
     flight and returns; the solve reports EIK_ERR_TIMEOUT and the GPU context
     stays usable for the next solve."""
@@ -170,12 +170,10 @@ def test_bounded_wait_timeout_is_reported(eik):
 
 
 @pytest.mark.parametrize("ndim,tile_override", [
-    (2, 1), (2, 2), (2, 3), (2, 4), (2, 5), (2, 6), (2, 7), (2, 10), (2, 11), (2, 12),
-    (3, 1), (3, 8), (3, 9)])
+    (2, 0), (2, 1), (2, 2), (2, 3), (2, 4), (3, 0), (3, 1), (3, 2), (3, 3), (3, 4)])
 def test_kernel_variants_agree_with_oracle(eik, ndim, tile_override):
-    """Every inner-CG kernel variant (generic halo tiles, warp-marched rows,
-    TMA-staged tiles of each shape and depth, 3D z-marching) meets the S
-    bound on a grid whose nx admits all of them."""
+    """Every inner-CG kernel variant (2D: warps per block and stage depth;
+    3D: rows per tile and plane stages) meets the S bound."""
     inst = wl.config2(n=264) if ndim == 2 else wl.config3(n=40)
     import torch
     opt = eik.make_options(precision="mixed", tol=1e-9, tile_override=tile_override)
@@ -187,12 +185,13 @@ def test_kernel_variants_agree_with_oracle(eik, ndim, tile_override):
     assert np.max(np.abs(S.cpu().numpy().ravel() - S_ref)) <= S_ABS
 
 
-@pytest.mark.parametrize("dims,tile_override", [((263, 131), 6), ((263, 131), 10),
-                                                ((41, 23, 19), 8), ((41, 23, 19), 9)])
+@pytest.mark.parametrize("dims,tile_override", [((263, 131), 1), ((263, 131), 4),
+                                                ((130, 7), 3), ((41, 23, 19), 1),
+                                                ((41, 23, 19), 3), ((131, 5, 9), 2)])
 def test_tma_kernels_on_odd_widths(eik, dims, tile_override):
-    """The TMA kernels on grids whose width is not a multiple of 8: the FP32
-    arrays get a padded row pitch (and the last node of a row can be the
-    first of a lane's pair)."""
+    """The inner-CG kernels on grids whose width is not a multiple of 4 (the
+    FP32 arrays get a padded row pitch), with ragged last tiles in every
+    direction and tiles wider or taller than the grid."""
     import torch
     rng = np.random.default_rng(sum(dims))
     h = 1.0 / (max(dims) - 1)
