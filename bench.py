@@ -83,6 +83,9 @@ def parse():
     ap.add_argument("--tile-override", type=int, default=0,
                     help="inner-CG kernel variant (eik_options.tile_override): 0 library "
                          "choice, 1..4 the variants listed in include/eik.h")
+    ap.add_argument("--modes", default="both", choices=["both", "one"],
+                    help="single-grid workloads: time both precision modes (default) or only "
+                         "--precision (shorter profiler captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=0,
@@ -262,7 +265,9 @@ def run_ours(args):
                                band_bits=args.band_bits, inner_tol=args.inner_tol)
         return eik.eik_create(inst.dims, inst.h, inst.hbar, f_dev, src, None, opt)
 
-    modes = [args.precision] + [m for m in ("fp64", "mixed") if m != args.precision]
+    modes = [args.precision]
+    if args.modes == "both":
+        modes += [m for m in ("fp64", "mixed") if m != args.precision]
     results = {}
     S_dev = torch.empty(inst.dims[::-1], dtype=torch.float64, device="cuda")
     for mode in modes:

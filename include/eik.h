@@ -92,8 +92,8 @@ typedef struct {
                          to rounding; for tuning and tests):
                          0 = library choice (variant 1);
                          2D (every warp an independent pipeline over tiles
-                         of 128 columns): 1..4 = (warps per block, row
-                         stages per warp) = (8, 8), (8, 6), (4, 8), (4, 12);
+                         of 128 columns): 1..4 = (row stages per warp,
+                         warps per block) = (5, 5), (6, 4), (7, 4), (6, 7);
                          3D (a block marches 128 x TY rows through z):
                          1..4 = (TY, plane stages) = (8, 4), (12, 4), (4, 4),
                          (8, 3).  Other values return EIK_ERR_ARG. */

@@ -51,7 +51,6 @@ __device__ __forceinline__ double acc_ratio(const Acc &a, const Acc &b) {
 template <bool INIT>
 __device__ void cg_tail(float gam, float dlt, float rmax, float pmax, int bad, bool fault,
                         MixCtl *st, double *part, int nblk_part) {
-  __shared__ double sh[32];
   __shared__ int flag;
   for (int o = 16; o > 0; o >>= 1) {
     gam += __shfl_down_sync(0xffffffffu, gam, o);
@@ -90,12 +89,48 @@ __device__ void cg_tail(float gam, float dlt, float rmax, float pmax, int bad, b
     if (fault) atomicExch(&st->fault, 1);
   }
   if (!last_block(&st->counter[1], &flag)) return;
-  const double G = sum_partials(part, gridDim.x, sh);
-  const double D = sum_partials(part + nblk_part, gridDim.x, sh);
-  const double R = max_partials(part + 2 * nblk_part, gridDim.x, sh);
-  const double P = max_partials(part + 3 * nblk_part, gridDim.x, sh);
-  const double Bd = max_partials(part + 4 * nblk_part, gridDim.x, sh);
+  // the five partial arrays in one round: every load is issued before any
+  // is used, then one shuffle tree and one shared-memory step per quantity
+  double G = 0.0, D = 0.0, R = 0.0, P = 0.0, Bd = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    const double g0 = __ldcg(part + b), d0 = __ldcg(part + nblk_part + b);
+    const double r0 = __ldcg(part + 2 * nblk_part + b), p0 = __ldcg(part + 3 * nblk_part + b);
+    const double b0 = __ldcg(part + 4 * nblk_part + b);
+    G += g0;
+    D += d0;
+    R = fmax(R, r0);
+    P = fmax(P, p0);
+    Bd = fmax(Bd, b0);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    G += __shfl_down_sync(0xffffffffu, G, o);
+    D += __shfl_down_sync(0xffffffffu, D, o);
+    R = fmax(R, __shfl_down_sync(0xffffffffu, R, o));
+    P = fmax(P, __shfl_down_sync(0xffffffffu, P, o));
+    Bd = fmax(Bd, __shfl_down_sync(0xffffffffu, Bd, o));
+  }
+  __shared__ double tg[32], td[32], tr[32], tp[32], tb[32];
+  if (lane == 0) {
+    tg[w] = G;
+    td[w] = D;
+    tr[w] = R;
+    tp[w] = P;
+    tb[w] = Bd;
+  }
+  __syncthreads();
   if (threadIdx.x != 0) return;
+  G = 0.0;
+  D = 0.0;
+  R = 0.0;
+  P = 0.0;
+  Bd = 0.0;
+  for (int k = 0; k < nwarp; ++k) {   // fixed order: deterministic
+    G += tg[k];
+    D += td[k];
+    R = fmax(R, tr[k]);
+    P = fmax(P, tp[k]);
+    Bd = fmax(Bd, tb[k]);
+  }
   st->counter[1] = 0u;
   const int F = st->F, dF = st->dF, fd = st->fd;
   const Acc gam_new = acc_of(G, 2 * F + fd);
@@ -167,26 +202,99 @@ __device__ void cg_tail(float gam, float dlt, float rmax, float pmax, int bad, b
 }
 
 // ------------------------------------------------------------------ 2D pass
-// One warp owns tiles of 128 columns x TY rows.  The tile's rows, with a
-// two-row halo, stream through a ring of NS shared-memory stages, one TMA row
-// copy (136 columns from x0 - 4) per array and stage.  Lane l holds columns
-// x0 + 4l .. x0 + 4l + 3; lanes 0 and 31 also carry the halo columns
-// x0 - 2, x0 - 1 and x0 + 128, x0 + 129.  At step j (input row y_j):
-//   row y_j:       p = r + beta p, u = sig p            (stage A)
-//   row y_{j-1}:   s = A p, r_new = r - alpha s, un = sig r_new   (stage B)
-//   row y_{j-2}:   w = A r_new, the dots, d += alpha p, stores    (stage C)
-// Odd tile rows march upwards, so the halo rows two neighbouring tiles share
-// are read at the same time (and come from L2 the second time).
+// One warp owns tiles of 128 columns x TY rows and runs them as its own
+// pipeline: the tile's rows (with a two-row halo) arrive by one TMA row copy
+// per array (r, p, sigma: 136 columns from x0 - 4) into a ring of NS stages,
+// and d (and, in checking passes, the FP32 iterate) of the tile's rows come
+// two steps ahead by plain vector loads.  At step j (input row y_j):
+//   A, row y_j:      p = r + beta p, written back to the stage
+//   B, row y_{j-1}:  u = sig p of rows y_{j-2} .. y_j, s = A p,
+//                    r_new = r - alpha s, un = sig r_new into a four-row ring
+//   C, row y_{j-2}:  w = A r_new, the dots, d += alpha p, stores
+// Lane l computes columns x0 + 4l .. x0 + 4l + 3, and lanes 0 and 31 also the
+// halo columns (A: x0 - 2, x0 - 1 / x0 + 128, x0 + 129; B: x0 - 1 / x0 + 128)
+// that neighbouring columns read.  A stage is free once C has used it, two
+// steps after A, so NS - 3 rows are in flight ahead of the one consumed.  Odd
+// tile rows march upwards, so the halo rows that two neighbouring tiles share
+// are read at about the same time.
+
+// Cell factors of one row for one lane: 2^(kx_i - kx_j) for the neighbours j
+// of the lane's columns i (and of its halo column), and the dot weight.
+struct Fac2 {
+  int cr;          // cell row of the row (INT_MIN: not computed)
+  int brd;         // the row is next to another cell row
+  float fL, fR;    // left neighbour of the first column, right of the last
+  float fP, fN;    // rows y - dir and y + dir
+  float fxh;       // halo column: its neighbour inside the tile
+  float fPh, fNh;  // halo column: rows y - dir and y + dir
+  float W;         // 2^(-2 kx - fd)
+};
+
+// Cell exponents of one tile's footprint, copied to shared memory at the
+// start of the tile (kTab entries per warp); tiles whose footprint does not
+// fit read kx from global memory instead.
+constexpr int kTab = 64;
+struct KTab {
+  const int *t;    // shared table, or nullptr: use kx in global memory
+  int cr0, cc0;    // first cell row and column of the table
+  int ncol;
+};
+
+__device__ __forceinline__ int ktab_at(const KTab &k, const int *__restrict__ kx,
+                                       const CellGrid &cg, int cr, int cc) {
+  return k.t ? k.t[(cr - k.cr0) * k.ncol + (cc - k.cc0)] : __ldg(kx + cr * cg.cx + cc);
+}
+
+__device__ __forceinline__ void fac2_update(Fac2 &f, int y, int dir, const Grid &g,
+                                            const CellGrid &cg, const int *__restrict__ kx,
+                                            const KTab &kt, int cxo, int cxl, int cxr, int cxh,
+                                            int fd) {
+  const int cr = min(max(y, 0), g.ny - 1) >> cg.lgB;
+  const int cp = min(max(y - dir, 0), g.ny - 1) >> cg.lgB;
+  const int cn = min(max(y + dir, 0), g.ny - 1) >> cg.lgB;
+  const int brd = (cp != cr) || (cn != cr);
+  if (cr == f.cr && !brd && !f.brd) return;   // same cell row, interior rows
+  const int kc = ktab_at(kt, kx, cg, cr, cxo), kh = ktab_at(kt, kx, cg, cr, cxh);
+  f.fL = p2f(kc - ktab_at(kt, kx, cg, cr, cxl));
+  f.fR = p2f(kc - ktab_at(kt, kx, cg, cr, cxr));
+  f.fxh = p2f(kh - kc);
+  if (brd) {
+    f.fP = p2f(kc - ktab_at(kt, kx, cg, cp, cxo));
+    f.fN = p2f(kc - ktab_at(kt, kx, cg, cn, cxo));
+    f.fPh = p2f(kh - ktab_at(kt, kx, cg, cp, cxh));
+    f.fNh = p2f(kh - ktab_at(kt, kx, cg, cn, cxh));
+  } else {
+    f.fP = f.fN = f.fPh = f.fNh = 1.f;
+  }
+  f.W = p2f(-2 * kc - fd);
+  f.cr = cr;
+  f.brd = brd;
+}
+
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void st4(float *p, float a, float b, float c, float d) {
+  *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ float4 mul4(const float4 &a, const float4 &b) {
+  return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w);
+}
+
 template <bool INIT, int NS, int WPB>
-__global__ void __launch_bounds__(32 * WPB, 1)
+__global__ void __launch_bounds__(32 * WPB)
 k_cg2d(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtensorMap tm_p,
        const __grid_constant__ CUtensorMap tm_s, Grid g, CellGrid cg,
        const int *__restrict__ kx, int tiles_x, int TY, int ntiles,
        float *__restrict__ r_out, float *__restrict__ p_out, float *__restrict__ d,
        const float *__restrict__ xref, MixCtl *st, double *part, int nblk_part, int px) {
-  constexpr int STAGE = 3 * kSlot;   // floats per stage: r, p, sigma rows
+  // stage: [r | p | sig] (kSlot floats each); ring row: [rn | un] (kWin each)
+  constexpr int OR = 0, OP = kSlot, OS = 2 * kSlot;
+  constexpr int STAGE = 3 * kSlot;
+  constexpr int RING = 2 * kWin;
+  constexpr int WARP_FLOATS = NS * STAGE + 4 * RING;
+  static_assert((STAGE * 4) % 128 == 0 && (WARP_FLOATS * 4) % 128 == 0, "stage alignment");
   extern __shared__ __align__(128) unsigned char cg2_raw[];
   __shared__ __align__(8) uint64_t bars[WPB * NS];
+  __shared__ int ktabs[WPB * kTab];
   if (st->done) return;
   float *cg2_smem = reinterpret_cast<float *>(
       (reinterpret_cast<uintptr_t>(cg2_raw) + 127) & ~uintptr_t(127));
@@ -204,28 +312,40 @@ k_cg2d(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtenso
   const int steps = TY + 4;
   const int my_tiles = (gw < ntiles) ? (ntiles - 1 - gw) / nw + 1 : 0;
   const int nq = my_tiles * steps;
-  float *sb = cg2_smem + (size_t)wib * NS * STAGE;
+  float *sb = cg2_smem + (size_t)wib * WARP_FLOATS;
+  float *ring = sb + NS * STAGE;
   uint64_t *bar = bars + wib * NS;
 
-  int next_issue = 0;   // lane 0: next row of the warp's sequence to copy
-  auto issue = [&](int q) {
-    const int k = q / steps, j = q - k * steps;
-    const int t = gw + k * nw;
+  // lane 0: the next row to copy, tracked incrementally (tile, step, origin)
+  int nx_q = 0, nx_j = 0, nx_x0 = 0, nx_y0 = 0, nx_dir = 1, nx_t = gw;
+  auto set_tile = [&](int t) {
+    nx_t = t;
     const int cyk = t / tiles_x;
-    const int x0 = (t - cyk * tiles_x) * kW;
-    const int y = (cyk & 1) ? (cyk * TY + TY + 1 - j) : (cyk * TY - 2 + j);
-    float *dst = sb + (q % NS) * STAGE;
-    uint64_t *b = bar + (q % NS);
-    mbar_expect_tx(b, (INIT ? 2u : 3u) * kWin * 4u);
-    tma_load_2d(dst, &tm_r, x0 - 4, y, b);
-    if (!INIT) tma_load_2d(dst + kSlot, &tm_p, x0 - 4, y, b);
-    tma_load_2d(dst + 2 * kSlot, &tm_s, x0 - 4, y, b);
+    nx_x0 = (t - cyk * tiles_x) * kW;
+    nx_y0 = cyk * TY;
+    nx_dir = (cyk & 1) ? -1 : 1;
+  };
+  auto issue_next = [&]() {
+    const int y = (nx_dir > 0) ? nx_y0 - 2 + nx_j : nx_y0 + TY + 1 - nx_j;
+    float *dst = sb + (nx_q % NS) * STAGE;
+    uint64_t *b = bar + (nx_q % NS);
+    if (!(nx_q == 0 && withhold)) {
+      mbar_expect_tx(b, (INIT ? 2u : 3u) * kWin * 4u);
+      tma_load_2d(dst + OR, &tm_r, nx_x0 - 4, y, b);
+      if (!INIT) tma_load_2d(dst + OP, &tm_p, nx_x0 - 4, y, b);
+      tma_load_2d(dst + OS, &tm_s, nx_x0 - 4, y, b);
+    }
+    ++nx_q;
+    if (++nx_j == steps) {
+      nx_j = 0;
+      set_tile(nx_t + nw);
+    }
   };
   if (lane == 0) {
     for (int k = 0; k < NS; ++k) mbar_init(&bar[k], 1);
     mbar_init_fence();
-    for (; next_issue < NS && next_issue < nq; ++next_issue)
-      if (!(next_issue == 0 && withhold)) issue(next_issue);
+    set_tile(gw);
+    while (nx_q < NS && nx_q < nq) issue_next();
   }
   __syncwarp();
 
@@ -233,6 +353,12 @@ k_cg2d(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtenso
   int bad = 0;
   bool fault = false;
   int q = 0;
+  const int c = 4 + 4 * lane;              // staged column of the lane's first node
+  const bool l0 = lane == 0, l31 = lane == 31;
+  const int hA = l31 ? kW + 4 : 2;         // A's halo pair x0-2, x0-1 / x0+128, x0+129
+  const int hB = l31 ? kW + 4 : 3;         // B's halo column x0-1 / x0+128
+  const int hI = l31 ? hB - 1 : hB + 1;    // its neighbour inside the tile
+  const int hO = l31 ? hB + 1 : hB - 1;    // and outside
   for (int k = 0; k < my_tiles && !fault; ++k) {
     const int t = gw + k * nw;
     const int cyk = t / tiles_x;
@@ -241,223 +367,177 @@ k_cg2d(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtenso
     const int dir = (cyk & 1) ? -1 : 1;
     const int ystart = (dir > 0) ? y0 - 2 : y0 + TY + 1;
     const int xl = x0 + 4 * lane;
-    const bool l31 = lane == 31;
     float hx[4];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) hx[c] = (half && (xl + c == 0 || xl + c == g.nx - 1)) ? 0.5f : 1.f;
-    const int xh = l31 ? x0 + kW : x0 - 1;   // inner halo column of lanes 0 / 31
+    for (int i = 0; i < 4; ++i) hx[i] = (half && (xl + i == 0 || xl + i == g.nx - 1)) ? 0.5f : 1.f;
+    const int xh = l31 ? x0 + kW : x0 - 1;
     const float hxh = (half && (xh == 0 || xh == g.nx - 1)) ? 0.5f : 1.f;
-    const int hcol = l31 ? kW + 4 : 2;       // staged column of the halo pair
-    // cell columns: own, of column xl - 1 and of column xl + 4 (clamped)
     const int cmax = cg.cx - 1;
     const int cxo = min(xl >> cg.lgB, cmax);
     const int cxl = (xl >= 1) ? min((xl - 1) >> cg.lgB, cmax) : cxo;
     const int cxr = (xl + 4 < g.nx) ? min((xl + 4) >> cg.lgB, cmax) : cxo;
-    const bool st_ok = xl < px;              // the float4 lies inside the row pitch
-
-    // ring registers (lag 0 = row y_j, 1 = y_{j-1}, ...)
-    float r0[4], p0[4], s0[4], u0[4];
-    float r1[4] = {0, 0, 0, 0}, p1[4] = {0, 0, 0, 0}, s1[4] = {0, 0, 0, 0},
-          u1[4] = {0, 0, 0, 0};
-    float p2[4] = {0, 0, 0, 0}, s2[4] = {0, 0, 0, 0}, u2[4] = {0, 0, 0, 0};
-    float rn1[4] = {0, 0, 0, 0}, rn2[4] = {0, 0, 0, 0};
-    float un1[4] = {0, 0, 0, 0}, un2[4] = {0, 0, 0, 0}, un3[4] = {0, 0, 0, 0};
-    float4 dq0 = make_float4(0, 0, 0, 0), dq1 = dq0, dq2 = dq0;
-    float4 xq0 = dq0, xq1 = dq0, xq2 = dq0;
-    float hr0, hp0, hs0, hu0, hou0;
-    float hr1 = 0, hp1 = 0, hs1 = 0, hu1 = 0, hou1 = 0, hu2 = 0;
-    float hun1 = 0, hun2 = 0;
-    int K0c = 0, K0l = 0, K0r = 0, K1c = 0, K1l = 0, K1r = 0, K2c = 0, K2l = 0, K2r = 0,
-        K3c = 0;
-    int cr_last = INT_MIN;
-    int kc_cache = 0, kl_cache = 0, kr_cache = 0;
+    const int cxh = l31 ? cxr : cxl;
+    const bool st_ok = xl < px;
+    Fac2 fb{INT_MIN, 0}, fc{INT_MIN, 0};
+    // the tile's cells (rows y0 - 3 .. y0 + TY + 2, columns x0 - 1 .. x0 + 128)
+    KTab kt{nullptr, 0, 0, 1};
+    {
+      const int cr0 = max(y0 - 3, 0) >> cg.lgB, cr1 = min(y0 + TY + 2, g.ny - 1) >> cg.lgB;
+      const int cc0 = max(x0 - 1, 0) >> cg.lgB, cc1 = min(min(x0 + kW, g.nx - 1) >> cg.lgB, cmax);
+      const int nrow = cr1 - cr0 + 1, ncol = cc1 - cc0 + 1;
+      __syncwarp();   // the previous tile's table is no longer read
+      if (nrow * ncol <= kTab) {
+        int *tab = ktabs + wib * kTab;
+        for (int e = lane; e < nrow * ncol; e += 32)
+          tab[e] = __ldg(kx + (cr0 + e / ncol) * cg.cx + cc0 + e % ncol);
+        __syncwarp();
+        kt = KTab{tab, cr0, cc0, ncol};
+      }
+    }
+    float4 dq0 = make_float4(0, 0, 0, 0), dq1 = dq0, dq2 = dq0;   // d of rows j, j-1, j-2
+    float4 xq0 = dq0, xq1 = dq0, xq2 = dq0;                       // xref likewise
 
     for (int j = 0; j < steps; ++j, ++q) {
-      // ---- row y_j from the stage
-      const int sidx = q % NS;
+      float *S0 = sb + (q % NS) * STAGE;
       // (a withheld first copy never lands: the bounded wait expires)
-      bool ok = mbar_wait_bounded(&bar[sidx], (uint32_t)(q / NS) & 1u);
+      bool ok = mbar_wait_bounded(&bar[q % NS], (uint32_t)(q / NS) & 1u);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) {
         fault = true;
         break;
       }
-      const float *S = sb + sidx * STAGE;
-      {
-        const float4 rv = *reinterpret_cast<const float4 *>(S + 4 + 4 * lane);
-        const float4 sv = *reinterpret_cast<const float4 *>(S + 2 * kSlot + 4 + 4 * lane);
-        const float2 rh = *reinterpret_cast<const float2 *>(S + hcol);
-        const float2 sh2 = *reinterpret_cast<const float2 *>(S + 2 * kSlot + hcol);
-        r0[0] = rv.x; r0[1] = rv.y; r0[2] = rv.z; r0[3] = rv.w;
-        s0[0] = sv.x; s0[1] = sv.y; s0[2] = sv.z; s0[3] = sv.w;
-        // lane 0: (.x, .y) = (outer x0-2, inner x0-1); lane 31: (inner, outer)
-        hr0 = l31 ? rh.x : rh.y;
-        hs0 = l31 ? sh2.x : sh2.y;
-        const float ro = l31 ? rh.y : rh.x, so = l31 ? sh2.y : sh2.x;
-        if (!INIT) {
-          const float4 pv = *reinterpret_cast<const float4 *>(S + kSlot + 4 + 4 * lane);
-          const float2 ph = *reinterpret_cast<const float2 *>(S + kSlot + hcol);
-          p0[0] = fmaf(beta, pv.x, r0[0]);
-          p0[1] = fmaf(beta, pv.y, r0[1]);
-          p0[2] = fmaf(beta, pv.z, r0[2]);
-          p0[3] = fmaf(beta, pv.w, r0[3]);
-          hp0 = fmaf(beta, l31 ? ph.x : ph.y, hr0);
-          hou0 = so * fmaf(beta, l31 ? ph.y : ph.x, ro);
-        } else {
-          p0[0] = p0[1] = p0[2] = p0[3] = 0.f;
-          hp0 = 0.f;
-          hou0 = 0.f;
-        }
-        hu0 = hs0 * hp0;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) u0[c] = s0[c] * p0[c];
-      }
-      // every lane is done with the stage: it takes row q + NS
-      __syncwarp();
-      if (lane == 0 && next_issue < nq) {
-        fence_proxy_async();
-        issue(next_issue);
-        ++next_issue;
-      }
       const int y = ystart + dir * j;
-      // cell row of y_j (rows outside the grid use the nearest grid row)
-      {
-        const int cr = min(max(y, 0), g.ny - 1) >> cg.lgB;
-        if (cr != cr_last) {
-          cr_last = cr;
-          kc_cache = __ldg(kx + cr * cg.cx + cxo);
-          kl_cache = __ldg(kx + cr * cg.cx + cxl);
-          kr_cache = __ldg(kx + cr * cg.cx + cxr);
-        }
-        K0c = kc_cache;
-        K0l = kl_cache;
-        K0r = kr_cache;
-      }
-      // prefetch d (and xref) of an output row for stage C two steps on
-      const bool out_row = (j >= 2) && (j < TY + 2) && (y < g.ny);
-      if (!INIT && out_row && st_ok) {
+      // d (and xref) of an output row, used by stage C two steps on
+      if (!INIT && j >= 2 && j < TY + 2 && y < g.ny && st_ok) {
         const int64_t o = (int64_t)y * px + xl;
-        dq0 = *reinterpret_cast<const float4 *>(d + o);
+        dq0 = ld4(d + o);
         if (check) xq0 = __ldg(reinterpret_cast<const float4 *>(xref + o));
       }
-
-      // ---- stage B: row y_{j-1}
+      // ---- A: row y_j, p in place
+      if (!INIT) {
+        const float4 r4 = ld4(S0 + OR + c), p4 = ld4(S0 + OP + c);
+        st4(S0 + OP + c, fmaf(beta, p4.x, r4.x), fmaf(beta, p4.y, r4.y),
+            fmaf(beta, p4.z, r4.z), fmaf(beta, p4.w, r4.w));
+        if (l0 || l31) {
+          const float2 r2 = *reinterpret_cast<const float2 *>(S0 + OR + hA);
+          const float2 p2 = *reinterpret_cast<const float2 *>(S0 + OP + hA);
+          *reinterpret_cast<float2 *>(S0 + OP + hA) =
+              make_float2(fmaf(beta, p2.x, r2.x), fmaf(beta, p2.y, r2.y));
+        }
+      }
+      __syncwarp();
+      // ---- B: row y_{j-1}
       if (j >= 2) {
         const int y1 = y - dir;
+        const float *S1 = sb + ((q - 1) % NS) * STAGE;    // centre row
+        const float *S2 = sb + ((q - 2) % NS) * STAGE;    // row y1 - dir
+        float *RB = ring + ((q - 1) & 3) * RING;
         const float hy1 = (half && (y1 == 0 || y1 == g.ny - 1)) ? 0.5f : 1.f;
-        const int K1h = l31 ? K1r : K1l, K0h = l31 ? K0r : K0l, K2h = l31 ? K2r : K2l;
-        const float fL = p2f(K1c - K1l), fR = p2f(K1c - K1r);
-        const float fP = p2f(K1c - K2c), fN = p2f(K1c - K0c);
-        float uL = __shfl_up_sync(0xffffffffu, u1[3], 1);
-        float uR = __shfl_down_sync(0xffffffffu, u1[0], 1);
-        if (lane == 0) uL = hu1;
-        if (l31) uR = hu1;
-        const float xs[4] = {fmaf(uL, fL, u1[1]), u1[0] + u1[2], u1[1] + u1[3],
-                             fmaf(uR, fR, u1[2])};
+        const float4 r4 = ld4(S1 + OR + c), s4 = ld4(S1 + OS + c);
+        float rn[4];
+        const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
+        if (INIT) {
+          rn[0] = r4.x; rn[1] = r4.y; rn[2] = r4.z; rn[3] = r4.w;
+        } else {
+          fac2_update(fb, y1, dir, g, cg, kx, kt, cxo, cxl, cxr, cxh, fd);
+          const float4 p4 = ld4(S1 + OP + c);
+          const float4 uc = mul4(s4, p4);
+          const float4 up = mul4(ld4(S2 + OS + c), ld4(S2 + OP + c));
+          const float4 un = mul4(ld4(S0 + OS + c), ld4(S0 + OP + c));
+          const float uL = S1[OS + c - 1] * S1[OP + c - 1], uR = S1[OS + c + 4] * S1[OP + c + 4];
+          const float xs[4] = {fmaf(uL, fb.fL, uc.y), uc.x + uc.z, uc.y + uc.w,
+                               fmaf(uR, fb.fR, uc.z)};
+          const float ysP[4] = {up.x, up.y, up.z, up.w}, ysN[4] = {un.x, un.y, un.z, un.w};
+          const float pv[4] = {p4.x, p4.y, p4.z, p4.w}, rv[4] = {r4.x, r4.y, r4.z, r4.w};
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          if (INIT) {
-            rn1[c] = r1[c];
-          } else {
-            const float ys = fmaf(u2[c], fP, u0[c] * fN);
-            const float acc = fmaf(hy1, xs[c], hx[c] * ys);
-            const float sv = fmaf(-s1[c], acc, p1[c]);
-            rn1[c] = fmaf(-alpha, sv, r1[c]);
+          for (int i = 0; i < 4; ++i) {
+            const float ys = fmaf(ysP[i], fb.fP, ysN[i] * fb.fN);
+            const float acc = fmaf(hy1, xs[i], hx[i] * ys);
+            rn[i] = fmaf(-alpha, fmaf(-sv[i], acc, pv[i]), rv[i]);
           }
-          un1[c] = s1[c] * rn1[c];
         }
-        // halo column (lanes 0 / 31; other lanes compute a value nobody uses)
-        float hrn = hr1;
-        if (!INIT) {
-          const float uadj = l31 ? u1[3] : u1[0];
-          const float fxh = p2f(K1h - K1c), fPh = p2f(K1h - K2h), fNh = p2f(K1h - K0h);
-          const float acc = fmaf(hy1, fmaf(uadj, fxh, hou1), hxh * fmaf(hu2, fPh, hu0 * fNh));
-          hrn = fmaf(-alpha, fmaf(-hs1, acc, hp1), hr1);
+        st4(RB + c, rn[0], rn[1], rn[2], rn[3]);
+        st4(RB + kWin + c, sv[0] * rn[0], sv[1] * rn[1], sv[2] * rn[2], sv[3] * rn[3]);
+        if (l0 || l31) {
+          // the halo column x0 - 1 / x0 + 128
+          const float sh = S1[OS + hB];
+          float rh = S1[OR + hB];
+          if (!INIT) {
+            const float uin = S1[OS + hI] * S1[OP + hI];
+            const float uout = S1[OS + hO] * S1[OP + hO];
+            const float upv = S2[OS + hB] * S2[OP + hB], unv = S0[OS + hB] * S0[OP + hB];
+            const float acc = fmaf(hy1, fmaf(uin, fb.fxh, uout),
+                                   hxh * fmaf(upv, fb.fPh, unv * fb.fNh));
+            rh = fmaf(-alpha, fmaf(-sh, acc, S1[OP + hB]), rh);
+          }
+          RB[hB] = rh;
+          RB[kWin + hB] = sh * rh;
         }
-        hun1 = hs1 * hrn;
       }
-
-      // ---- stage C: row y_{j-2}
+      __syncwarp();
+      // ---- C: row y_{j-2}
       if (j >= 4) {
         const int y2 = y - 2 * dir;
         if (y2 < g.ny) {
+          fac2_update(fc, y2, dir, g, cg, kx, kt, cxo, cxl, cxr, cxh, fd);
+          const float *S2 = sb + ((q - 2) % NS) * STAGE;
+          const float *Rc = ring + ((q - 2) & 3) * RING;    // row y2
+          const float *Rp = ring + ((q - 3) & 3) * RING;    // row y2 - dir
+          const float *Rn = ring + ((q - 1) & 3) * RING;    // row y2 + dir
           const float hy2 = (half && (y2 == 0 || y2 == g.ny - 1)) ? 0.5f : 1.f;
-          const float fL = p2f(K2c - K2l), fR = p2f(K2c - K2r);
-          const float fP = p2f(K2c - K3c), fN = p2f(K2c - K1c);
-          const float W = p2f(-2 * K2c - fd);
-          float uL = __shfl_up_sync(0xffffffffu, un2[3], 1);
-          float uR = __shfl_down_sync(0xffffffffu, un2[0], 1);
-          if (lane == 0) uL = hun2;
-          if (l31) uR = hun2;
-          const float xs[4] = {fmaf(uL, fL, un2[1]), un2[0] + un2[2], un2[1] + un2[3],
-                               fmaf(uR, fR, un2[2])};
+          const float4 nc = ld4(Rc + kWin + c), np = ld4(Rp + kWin + c), nn = ld4(Rn + kWin + c);
+          const float4 rn4 = ld4(Rc + c), s4 = ld4(S2 + OS + c);
+          const float nL = Rc[kWin + c - 1], nR = Rc[kWin + c + 4];
+          const float xs[4] = {fmaf(nL, fc.fL, nc.y), nc.x + nc.z, nc.y + nc.w,
+                               fmaf(nR, fc.fR, nc.z)};
+          const float ysP[4] = {np.x, np.y, np.z, np.w}, ysN[4] = {nn.x, nn.y, nn.z, nn.w};
+          const float rv[4] = {rn4.x, rn4.y, rn4.z, rn4.w}, sv[4] = {s4.x, s4.y, s4.z, s4.w};
+          float pv[4] = {0, 0, 0, 0};
+          if (!INIT) {
+            const float4 p4 = ld4(S2 + OP + c);
+            pv[0] = p4.x; pv[1] = p4.y; pv[2] = p4.z; pv[3] = p4.w;
+          }
           const float dv[4] = {dq2.x, dq2.y, dq2.z, dq2.w};
           const float xv[4] = {xq2.x, xq2.y, xq2.z, xq2.w};
-          float dn[4], ro[4], po[4];
+          float dn[4];
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const float ys = fmaf(un3[c], fP, un1[c] * fN);
-            const float acc = fmaf(hy2, xs[c], hx[c] * ys);
-            const float wv = fmaf(-s2[c], acc, rn2[c]);
-            const float tt = rn2[c] * W;
-            gam = fmaf(tt, rn2[c], gam);
+          for (int i = 0; i < 4; ++i) {
+            const float ys = fmaf(ysP[i], fc.fP, ysN[i] * fc.fN);
+            const float acc = fmaf(hy2, xs[i], hx[i] * ys);
+            const float wv = fmaf(-sv[i], acc, rv[i]);
+            const float tt = rv[i] * fc.W;
+            gam = fmaf(tt, rv[i], gam);
             dlt = fmaf(tt, wv, dlt);
-            rmax = fmaxf(rmax, fabsf(rn2[c]));
-            if (!INIT) {
-              dn[c] = fmaf(alphaF, p2[c], dv[c]);
-              pmax = fmaxf(pmax, fabsf(p2[c]));
-              ro[c] = rn2[c] * gwr;
-              po[c] = p2[c] * gwr;
-              if (check && fabsf(rn2[c]) > thetaF * fabsf(xv[c] + dn[c])) bad = 1;
-            }
+            rmax = fmaxf(rmax, fabsf(rv[i]));
+            dn[i] = fmaf(alphaF, pv[i], dv[i]);
+            pmax = fmaxf(pmax, fabsf(pv[i]));
+            if (check && fabsf(rv[i]) > thetaF * fabsf(xv[i] + dn[i])) bad = 1;
           }
           if (!INIT && st_ok) {
             const int64_t o = (int64_t)y2 * px + xl;
-            *reinterpret_cast<float4 *>(d + o) = make_float4(dn[0], dn[1], dn[2], dn[3]);
-            *reinterpret_cast<float4 *>(r_out + o) = make_float4(ro[0], ro[1], ro[2], ro[3]);
-            *reinterpret_cast<float4 *>(p_out + o) = make_float4(po[0], po[1], po[2], po[3]);
+            st4(d + o, dn[0], dn[1], dn[2], dn[3]);
+            st4(r_out + o, rv[0] * gwr, rv[1] * gwr, rv[2] * gwr, rv[3] * gwr);
+            st4(p_out + o, pv[0] * gwr, pv[1] * gwr, pv[2] * gwr, pv[3] * gwr);
           }
         }
-      }
-
-      // ---- rotate the ring
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        un3[c] = un2[c];
-        un2[c] = un1[c];
-        rn2[c] = rn1[c];
-        p2[c] = p1[c];
-        s2[c] = s1[c];
-        u2[c] = u1[c];
-        r1[c] = r0[c];
-        p1[c] = p0[c];
-        s1[c] = s0[c];
-        u1[c] = u0[c];
       }
       dq2 = dq1;
       dq1 = dq0;
       xq2 = xq1;
       xq1 = xq0;
-      hun2 = hun1;
-      hu2 = hu1;
-      hr1 = hr0;
-      hp1 = hp0;
-      hs1 = hs0;
-      hu1 = hu0;
-      hou1 = hou0;
-      K3c = K2c;
-      K2c = K1c;
-      K2l = K1l;
-      K2r = K1r;
-      K1c = K0c;
-      K1l = K0l;
-      K1r = K0r;
+      // the stage of row q - 2 has been used for the last time: it takes
+      // the next row of the warp's sequence
+      __syncwarp();
+      if (l0 && q >= 2 && nx_q < nq) {
+        fence_proxy_async();
+        issue_next();
+      }
     }
   }
-  if (fault && lane == 0) {
+  if (fault && l0) {
     // leave no copy in flight: wait (bounded) for every row issued and not
     // yet waited for
-    for (int qq = q; qq < next_issue; ++qq)
+    for (int qq = q; qq < nx_q; ++qq)
       if (!(qq == 0 && withhold)) mbar_wait_bounded(&bar[qq % NS], (uint32_t)(qq / NS) & 1u);
   }
   __syncwarp();
@@ -846,7 +926,7 @@ bool encode_f32(CUtensorMap *map, void *base, int nx, int px, int ny, int nz, in
 // 2D variants: (warps per block, stages per warp)
 template <int NS, int WPB>
 size_t smem2d() {
-  return (size_t)WPB * NS * 3 * kSlot * sizeof(float) + 128;
+  return (size_t)WPB * (NS * 3 * kSlot + 4 * 2 * kWin) * sizeof(float) + 128;
 }
 
 template <int NS, int WPB>
@@ -894,28 +974,29 @@ void launch2d_t(const Cg32Plan &pl, const Grid &g, const CellGrid &cg, const Cg3
                 int set, cudaStream_t s) {
   const int a = set, o = 1 - set;
   k_cg2d<INIT, NS, WPB><<<pl.nblk, 32 * WPB, pl.smem, s>>>(
-      pl.tm_r[a], pl.tm_p[a], pl.tm_s, g, cg, b.kx, pl.tiles_x, pl.ty, pl.ntiles, b.r[o], b.p[o],
-      b.d, b.xref, b.st, b.part, b.nblk_part, b.px);
+      pl.tm_r[a], pl.tm_p[a], pl.tm_s, g, cg, b.kx, pl.tiles_x, pl.ty, pl.ntiles, b.r[o],
+      b.p[o], b.d, b.xref, b.st, b.part, b.nblk_part, b.px);
 }
 
-// 2D variant table: 1 = (8 stages, 8 warps), 2 = (6, 8), 3 = (8, 4), 4 = (12, 4)
+// 2D variant table (stages per warp, warps per block):
+// 1 = (5, 5), 2 = (6, 4), 3 = (7, 4), 4 = (6, 7)
 template <bool INIT>
 void launch2d(const Cg32Plan &pl, const Grid &g, const CellGrid &cg, const Cg32Buffers &b,
               int set, cudaStream_t s) {
   switch (pl.variant) {
-    case 2: launch2d_t<INIT, 6, 8>(pl, g, cg, b, set, s); break;
-    case 3: launch2d_t<INIT, 8, 4>(pl, g, cg, b, set, s); break;
-    case 4: launch2d_t<INIT, 12, 4>(pl, g, cg, b, set, s); break;
-    default: launch2d_t<INIT, 8, 8>(pl, g, cg, b, set, s); break;
+    case 2: launch2d_t<INIT, 6, 4>(pl, g, cg, b, set, s); break;
+    case 3: launch2d_t<INIT, 7, 4>(pl, g, cg, b, set, s); break;
+    case 4: launch2d_t<INIT, 6, 7>(pl, g, cg, b, set, s); break;
+    default: launch2d_t<INIT, 5, 5>(pl, g, cg, b, set, s); break;
   }
 }
 
 bool plan2d(Cg32Plan *pl, const Grid &g, int num_sms) {
   switch (pl->variant) {
-    case 2: return plan2d_t<6, 8>(pl, g, num_sms);
-    case 3: return plan2d_t<8, 4>(pl, g, num_sms);
-    case 4: return plan2d_t<12, 4>(pl, g, num_sms);
-    default: pl->variant = 1; return plan2d_t<8, 8>(pl, g, num_sms);
+    case 2: return plan2d_t<6, 4>(pl, g, num_sms);
+    case 3: return plan2d_t<7, 4>(pl, g, num_sms);
+    case 4: return plan2d_t<6, 7>(pl, g, num_sms);
+    default: pl->variant = 1; return plan2d_t<5, 5>(pl, g, num_sms);
   }
 }
 
