@@ -44,6 +44,10 @@ ALGO_BYTES_PER_NODE = {
     # in later refinement steps) also read the FP32 iterate, not counted
     "mixed_cg": 28,
     "mixed_cg_init": 8,  # first pass of an inner solve: read r, sig
+    # FP64 residual of a refinement step: read sig, x (f64); write r, p, d,
+    # xref (f32)
+    "mixed_residual64": 32,
+    "mixed_update": 20,  # read d (f32), read and write x (f64)
 }
 
 # The FP64 passes are bound by the FP64 pipe, not by HBM: their roofline is
@@ -86,6 +90,8 @@ def parse():
     ap.add_argument("--modes", default="both", choices=["both", "one"],
                     help="single-grid workloads: time both precision modes (default) or only "
                          "--precision (shorter profiler captures)")
+    ap.add_argument("--no-c3-block", action="store_true",
+                    help="default 2D workload: skip timing the 3D 256^3 workload beside it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=0,
@@ -246,13 +252,26 @@ def run_ours(args):
     from paper_1403_1937_gb300 import build as _build
     if not _build.up_to_date():
         _build.build()
-    from paper_1403_1937_gb300 import eik
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     if ws > 1:
         dist.init_process_group("nccl")
-    inst, desc = workload(args.workload)
+    inst, desc, n_unk, results = measure(args, args.workload, ws, local)
+    if ws > 1:
+        dist.barrier()
+    return inst, desc, n_unk, results, ws, rank
+
+
+def measure(args, wname, ws, local, modes=None):
+    """Times one single-grid workload in the requested precision modes:
+    device-resident steps (set_f + solve, L2 flushed between steps), the same
+    through host buffers (e2e), and one step with per-launch CUDA events."""
+    import torch
+    import torch.distributed as dist
+    from paper_1403_1937_gb300 import eik
+
+    inst, desc = workload(wname)
     n_unk = inst.n - len(np.unique(inst.src_idx))
     f_host = torch.from_numpy(np.ascontiguousarray(inst.f)).pin_memory()
     f_dev = f_host.cuda()
@@ -265,15 +284,16 @@ def run_ours(args):
                                band_bits=args.band_bits, inner_tol=args.inner_tol)
         return eik.eik_create(inst.dims, inst.h, inst.hbar, f_dev, src, None, opt)
 
-    modes = [args.precision]
-    if args.modes == "both":
-        modes += [m for m in ("fp64", "mixed") if m != args.precision]
+    if modes is None:
+        modes = [args.precision]
+        if args.modes == "both":
+            modes += [m for m in ("fp64", "mixed") if m != args.precision]
     results = {}
     S_dev = torch.empty(inst.dims[::-1], dtype=torch.float64, device="cuda")
     for mode in modes:
         try:
             hd = make(mode)
-        except Exception as e:  # mixed may be unavailable in this build
+        except Exception as e:  # a mode the build cannot run
             results[mode] = {"error": str(e).splitlines()[0]}
             continue
         if args.per_launch:
@@ -331,9 +351,50 @@ def run_ours(args):
                             for k, v in prof.items() if v[0]}
         results[mode] = res
         eik.eik_destroy(hd)
-    if ws > 1:
-        dist.barrier()
-    return inst, desc, n_unk, results, ws, rank
+    return inst, desc, n_unk, results
+
+
+def kernel_table(res, inst):
+    """Per-kernel figures of the timed step: average launch time and, where
+    the algorithmic bytes per node are known, achieved GB/s and the fraction
+    of the measured HBM bandwidth."""
+    peak, _ = measured_peaks()
+    out = {}
+    for k, (avg_ms, n, tot) in sorted(res.get("kernel_ms", {}).items()):
+        if avg_ms is None:
+            continue
+        e = {"avg_us": round(avg_ms * 1e3, 2), "timed_launches": n}
+        if k in ALGO_BYTES_PER_NODE:
+            gbs = ALGO_BYTES_PER_NODE[k] * inst.n / (avg_ms * 1e-3) / 1e9
+            e["achieved_gbs"] = round(gbs, 1)
+            e["frac_of_hbm"] = round(gbs / peak, 4)
+        out[k] = e
+    return out
+
+
+def secondary_block(args, ws, local):
+    """The 3D 256^3 workload timed in the same run as the headline 2D one:
+    both precision modes, their ratio and the rooflines of the inner-CG
+    kernels (no CPU baseline, no e2e)."""
+    saved = args.no_e2e
+    args.no_e2e = True
+    inst, desc, n_unk, res = measure(args, "c3", ws, local, modes=["mixed", "fp64"])
+    args.no_e2e = saved
+    out = {"workload": desc["workload"]}
+    for mode, r in res.items():
+        if "glups" in r:
+            out[mode] = {"glups": round(r["glups"], 3), "ms_per_step": round(r["ms_per_step"], 3),
+                         "cg_iters_per_step": r["cg_iters_per_step"],
+                         "res_cw": r["stats_last"]["res_cw"],
+                         "kernels": kernel_table(r, inst)}
+        else:
+            out[mode] = r
+    if "glups" in res.get("fp64", {}) and "glups" in res.get("mixed", {}):
+        out["mixed_speedup_vs_fp64"] = round(
+            res["fp64"]["ms_per_step"] / res["mixed"]["ms_per_step"], 3)
+        out["roofline"] = roofline(res["mixed"], inst, "c3")
+        out["clocks"] = res["mixed"]["clocks"]
+    return out
 
 
 def run_diff(args):
@@ -574,6 +635,9 @@ def main():
         run_diff(args)
         return
     inst, desc, n_unk, results, ws, rank = run_ours(args)
+    c3 = None
+    if args.workload == "c2" and not args.no_c3_block:
+        c3 = secondary_block(args, ws, int(os.environ.get("LOCAL_RANK", "0")))
     if rank != 0:
         return
     head = results.get(args.precision, {})
@@ -611,7 +675,10 @@ def main():
         "roofline": roofline(head, inst, args.workload),
         "cpu_baseline": cpu,
         "comparison": comparison,
+        "kernels": kernel_table(head, inst),
     }
+    if c3 is not None:
+        line["c3"] = c3
     print(json.dumps(line), flush=True)
 
 

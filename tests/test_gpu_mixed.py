@@ -48,6 +48,18 @@ def test_c1_mixed(eik):
     assert kst["cg_pass1_64"][0] == 0      # the FP64 CG did not run
 
 
+def test_c1_mixed_bench_tolerance(eik):
+    """Config 1 in mixed precision at the bench's componentwise tolerance
+    1e-6: S within 1e-6 of the direct oracle everywhere (including the far
+    corners, where phi ~ 1e-31)."""
+    inst = wl.config1()
+    S, _, stats, _ = mixed_solve(eik, inst, tol=1e-6)
+    S_ref, _, _ = fd.solve(inst.f, inst.dims, inst.h, inst.hbar, inst.src_idx)
+    assert stats["res_cw"] <= 1e-6
+    assert np.max(np.abs(S - S_ref)) <= S_ABS
+    assert S[inst.src_idx[0]] == 0.0
+
+
 @pytest.mark.parametrize("seed,ndim,boundary,with_U", [
     (0, 2, "half_cell", False), (1, 2, "drop_edge", True), (2, 3, "half_cell", False),
     (3, 3, "half_cell", True), (4, 2, "half_cell", False),
