@@ -160,19 +160,26 @@ def c4_sample(insts, count=32):
 def test_full_batch_sample_vs_oracle(eik):
     """32 instances of the full 256-instance batched workload (both ends of
     the size range, every hbar/h, the widest S/hbar ranges, which need the
-    level-set sweep), solved together through the batch API, against the
-    oracle's relative-form direct solve (phi itself underflows float64)."""
+    level-set sweep), solved together through the batch API at the bench's
+    tolerance for this workload (componentwise 1e-7), against the oracle's
+    relative-form direct solve (phi itself underflows float64).
+
+    Why 1e-7: with hbar = 8h the smallest eigenvalue of the Jacobi-scaled
+    operator is about (f h / hbar)^2 / 4, so smooth error components pass a
+    componentwise residual test with a relative phi error a few hundred times
+    larger; at 1e-6 one instance (230, 914 x 926) met the residual test with
+    S off by 2.9e-6."""
     insts = wl.config4()
     pick = c4_sample(insts)
     assert len(pick) == 32
     sub = [insts[k] for k in pick]
     assert {round(i.hbar / i.h) for i in sub} == {2, 4, 8}
-    opt = eik.make_options(precision="mixed", tol=1e-6)
+    opt = eik.make_options(precision="mixed", tol=1e-7)
     b = eik.eik_create_batch(sub, opt)
     S, stats = eik.eik_solve_batch(b)
     parts = b.split(S.cpu().numpy())
     for k, inst, Si, st in zip(pick, sub, parts, stats):
-        assert st["res_cw"] <= 1e-6, k
+        assert st["res_cw"] <= 1e-7, k
         sys = fd.assemble(inst.f, inst.dims, inst.h, inst.hbar, inst.src_idx)
         S_ref = fd.solve_relative(sys)
         assert np.max(np.abs(Si.ravel() - S_ref)) <= 1e-6, k
