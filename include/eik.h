@@ -95,8 +95,9 @@ typedef struct {
                          of 128 columns): 1..4 = (row stages per warp,
                          warps per block) = (5, 5), (6, 4), (7, 4), (6, 7);
                          3D (a block marches 128 x TY rows through z):
-                         1..4 = (TY, plane stages) = (8, 4), (12, 4), (4, 4),
-                         (8, 3).  Other values return EIK_ERR_ARG. */
+                         1..4 = (TY, plane stages) = (12, 5), (8, 6),
+                         (16, 4), (8, 8).  Other values return
+                         EIK_ERR_ARG. */
   double inner_tol;   /* mixed mode: factor by which the first FP32 inner
                          solve of a refinement step reduces the residual
                          (scaled max norm); 0 = library choice (1e-1) */

@@ -548,16 +548,24 @@ k_cg2d(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtenso
 // A block owns tiles of 128 columns x TY rows x zc planes and marches them
 // through z.  Each plane of r, p and sigma arrives by one TMA copy per array
 // (box 136 x (TY + 4) x 1 from (x0 - 4, y0 - 2, z)) into a ring of NS
-// stages.  Warp w owns row y0 - 2 + w (TY + 4 warps) with lanes as in 2D.  At
-// plane step j (plane z_j):
-//   every warp, plane z_j:               p = r + beta p, u = sig p      (A)
-//   warps 1 .. TY + 2, plane z_{j-1}:    s = A p, r_new, un = sig r_new (B)
-//   warps 2 .. TY + 1, plane z_{j-2}:    w = A r_new, dots, d, stores   (C)
-// The z neighbours of a node are in its own thread's registers, the x
-// neighbours come by warp shuffle, the y neighbours through two shared rings
-// (u of the last plane, un of the last plane); one block barrier per step
-// orders them.  Odd z chunks march downwards (shared halo planes are read by
-// both neighbours at the same time).
+// stages, and stays there until consumed.  Warp w owns row y0 - 2 + w (TY + 4
+// warps), lanes as in 2D.  At plane step j (plane z_j):
+//   A, every warp, plane z_j:            p = r + beta p, in place
+//   B, warps 1 .. TY + 2, plane z_{j-1}: u = sig p of the node and its six
+//        neighbours, s = A p, r_new, un = sig r_new; r_new, sig, p of the
+//        plane go to a two-plane ring and un to a three-plane ring
+//   C, warps 2 .. TY + 1, plane z_{j-2}: w = A r_new, the dots,
+//        d += alpha p, stores
+// B takes the y and x neighbours from the stage of its plane (written by A
+// one step earlier) and its own column's u of planes z_j and z_{j-2} from
+// registers; C reads only the rings.  One block barrier per step orders the
+// steps.  So a stage is free one step after A, and NS - 2 planes beyond the
+// current one are in flight.  Measured, a step of the (12, 5) block costs
+// about the same whatever NS: the pass is bound by the latency of one block
+// step (the barrier and the shared-memory round trips of A, B, C), which is
+// why taller tiles (fewer steps, more warps per barrier) do not help either.
+// Odd z chunks march downwards, so the halo planes two neighbouring chunks
+// share are read at about the same time.
 __device__ __forceinline__ int cell_k(const CellGrid &cg, const int *__restrict__ kx, int cxi,
                                       int y, int z, const Grid &g) {
   const int cy = min(max(y, 0), g.ny - 1) >> cg.lgB;
@@ -574,15 +582,15 @@ k_cg3d(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtenso
        const float *__restrict__ xref, MixCtl *st, double *part, int nblk_part, int px) {
   constexpr int NR = TY + 4;             // staged rows
   constexpr int PLANE = NR * kWin;       // floats per array and plane
-  constexpr int STAGE = 3 * PLANE;
+  constexpr int STAGE = 3 * PLANE;       // r, p, sigma
   static_assert((PLANE * 4) % 128 == 0, "plane size");
   extern __shared__ __align__(128) unsigned char cg3_raw[];
   __shared__ __align__(8) uint64_t bars[NS];
   if (st->done) return;
   float *cg3_smem = reinterpret_cast<float *>(
       (reinterpret_cast<uintptr_t>(cg3_raw) + 127) & ~uintptr_t(127));
-  float *ring_u = cg3_smem + NS * STAGE;   // [2][NR][kWin]
-  float *ring_n = ring_u + 2 * PLANE;      // [2][NR][kWin]
+  float *ring_n = cg3_smem + NS * STAGE;   // un: [3 planes][NR][kWin]
+  float *ring_c = ring_n + 3 * PLANE;       // [2 planes][rn | sig | p][NR][kWin]
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const float beta = INIT ? 0.f : (float)st->beta;
   const float alpha = INIT ? 0.f : (float)st->alpha;
@@ -608,10 +616,12 @@ k_cg3d(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtenso
     const int z = (szc & 1) ? (szc * zc + zc + 1 - j) : (szc * zc - 2 + j);
     float *dst = cg3_smem + (q % NS) * STAGE;
     uint64_t *b = &bars[q % NS];
-    mbar_expect_tx(b, (INIT ? 2u : 3u) * PLANE * 4u);
-    tma_load_3d(dst, &tm_r, sx * kW - 4, sy * TY - 2, z, b);
-    if (!INIT) tma_load_3d(dst + PLANE, &tm_p, sx * kW - 4, sy * TY - 2, z, b);
-    tma_load_3d(dst + 2 * PLANE, &tm_s, sx * kW - 4, sy * TY - 2, z, b);
+    if (!(q == 0 && withhold)) {
+      mbar_expect_tx(b, (INIT ? 2u : 3u) * PLANE * 4u);
+      tma_load_3d(dst, &tm_r, sx * kW - 4, sy * TY - 2, z, b);
+      if (!INIT) tma_load_3d(dst + PLANE, &tm_p, sx * kW - 4, sy * TY - 2, z, b);
+      tma_load_3d(dst + 2 * PLANE, &tm_s, sx * kW - 4, sy * TY - 2, z, b);
+    }
   };
   if (threadIdx.x == 0) {
     for (int k = 0; k < NS; ++k) mbar_init(&bars[k], 1);
@@ -619,12 +629,16 @@ k_cg3d(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtenso
   }
   __syncthreads();
   if (threadIdx.x == 0)
-    for (; next_issue < NS && next_issue < nq; ++next_issue)
-      if (!(next_issue == 0 && withhold)) issue(next_issue);
+    for (; next_issue < NS && next_issue < nq; ++next_issue) issue(next_issue);
 
   const bool doB = (w >= 1 && w <= TY + 2), doC = (w >= 2 && w <= TY + 1);
-  const bool l31 = lane == 31;
-  const int hcol = l31 ? kW + 4 : 2;
+  const bool l0 = lane == 0, l31 = lane == 31;
+  const int c = 4 + 4 * lane;                 // staged column of the lane's first node
+  const int hA = l31 ? kW + 4 : 2;            // A's halo pair
+  const int hB = l31 ? kW + 4 : 3;            // B's halo column
+  const int hI = l31 ? hB - 1 : hB + 1;       // its neighbour inside the tile
+  const int hO = l31 ? hB + 1 : hB - 1;       // and outside
+  const int rw = w * kWin;                    // the warp's row in a plane
   float gam = 0.f, dlt = 0.f, rmax = 0.f, pmax = 0.f;
   int bad = 0;
   bool fault = false;
@@ -639,7 +653,7 @@ k_cg3d(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtenso
     const int xl = x0 + 4 * lane;
     float hx[4];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) hx[c] = (half && (xl + c == 0 || xl + c == g.nx - 1)) ? 0.5f : 1.f;
+    for (int i = 0; i < 4; ++i) hx[i] = (half && (xl + i == 0 || xl + i == g.nx - 1)) ? 0.5f : 1.f;
     const int xh = l31 ? x0 + kW : x0 - 1;
     const float hxh = (half && (xh == 0 || xh == g.nx - 1)) ? 0.5f : 1.f;
     const float hy = (half && (y == 0 || y == g.ny - 1)) ? 0.5f : 1.f;
@@ -650,26 +664,17 @@ k_cg3d(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtenso
     const int cxh = l31 ? cxr : cxl;
     const bool row_ok = y >= 0 && y < g.ny;
     const bool st_ok = xl < px && row_ok;
-
-    float r0[4], p0[4], s0[4], u0[4];
-    float r1[4] = {0, 0, 0, 0}, p1[4] = {0, 0, 0, 0}, s1[4] = {0, 0, 0, 0},
-          u1[4] = {0, 0, 0, 0};
-    float p2[4] = {0, 0, 0, 0}, s2[4] = {0, 0, 0, 0}, u2[4] = {0, 0, 0, 0};
-    float rn1[4] = {0, 0, 0, 0}, rn2[4] = {0, 0, 0, 0};
-    float un1[4] = {0, 0, 0, 0}, un2[4] = {0, 0, 0, 0}, un3[4] = {0, 0, 0, 0};
-    float4 dq0 = make_float4(0, 0, 0, 0), dq1 = dq0, dq2 = dq0;
-    float4 xq0 = dq0, xq1 = dq0, xq2 = dq0;
-    float hr0, hp0, hs0, hu0, hou0;
-    float hr1 = 0, hp1 = 0, hs1 = 0, hu1 = 0, hou1 = 0, hu2 = 0, hun1 = 0, hun2 = 0;
-    // cell exponents: own column (lags 0..3), halo column (lags 0..2)
-    int K0 = 0, K1 = 0, K2 = 0, K3 = 0, H0 = 0, H1 = 0, H2 = 0;
-    // x / y factors, recomputed when a stage's plane enters another cell layer
-    int lay_B = INT_MIN, lay_C = INT_MIN, lay_A = INT_MIN;
-    float bL = 1, bR = 1, bS = 1, bN = 1, bxh = 1, bhS = 1, bhN = 1;
-    float cL = 1, cR = 1, cS = 1, cN = 1, cW = 0;
-    int kA = 0, hA = 0;
-
-    for (int j = 0; j < steps; ++j, ++q) {
+    // cell factors of stage B (plane z_{j-1}) and C (plane z_{j-2}), cached
+    // per cell layer; z factors are 1 except next to another layer
+    int layB = INT_MIN, layC = INT_MIN;
+    float bL = 1, bR = 1, bS = 1, bN = 1, bP = 1, bNz = 1, bxh = 1, bhS = 1, bhN = 1, bhP = 1,
+          bhNz = 1;
+    float cL = 1, cR = 1, cS = 1, cN = 1, cP = 1, cNz = 1, cW = 0;
+    float4 uA = make_float4(0, 0, 0, 0), uB = uA;     // own u of planes z_j, z_{j-1}
+    float4 uBp = uA;                                  // own u of plane z_{j-2}
+    float hA0 = 0.f, hB0 = 0.f, hBp = 0.f;            // the same for the halo column
+    float4 dq0 = uA, dq1 = uA, dq2 = uA, xq0 = uA, xq1 = uA, xq2 = uA;
+    for (int j = 0; j < zc + 4; ++j, ++q) {
       const int sidx = q % NS;
       const bool okw = mbar_wait_bounded(&bars[sidx], (uint32_t)(q / NS) & 1u);
       if (__syncthreads_or(!okw)) {
@@ -677,205 +682,182 @@ k_cg3d(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtenso
         break;
       }
       const int z = zstart + dir * j;
-      const float *S = cg3_smem + sidx * STAGE + w * kWin;
-      // ---- A: plane z_j, row y
-      {
-        const float4 rv = *reinterpret_cast<const float4 *>(S + 4 + 4 * lane);
-        const float4 sv = *reinterpret_cast<const float4 *>(S + 2 * PLANE + 4 + 4 * lane);
-        const float2 rh = *reinterpret_cast<const float2 *>(S + hcol);
-        const float2 sh2 = *reinterpret_cast<const float2 *>(S + 2 * PLANE + hcol);
-        r0[0] = rv.x; r0[1] = rv.y; r0[2] = rv.z; r0[3] = rv.w;
-        s0[0] = sv.x; s0[1] = sv.y; s0[2] = sv.z; s0[3] = sv.w;
-        hr0 = l31 ? rh.x : rh.y;
-        hs0 = l31 ? sh2.x : sh2.y;
-        const float ro = l31 ? rh.y : rh.x, so = l31 ? sh2.y : sh2.x;
-        if (!INIT) {
-          const float4 pv = *reinterpret_cast<const float4 *>(S + PLANE + 4 + 4 * lane);
-          const float2 ph = *reinterpret_cast<const float2 *>(S + PLANE + hcol);
-          p0[0] = fmaf(beta, pv.x, r0[0]);
-          p0[1] = fmaf(beta, pv.y, r0[1]);
-          p0[2] = fmaf(beta, pv.z, r0[2]);
-          p0[3] = fmaf(beta, pv.w, r0[3]);
-          hp0 = fmaf(beta, l31 ? ph.x : ph.y, hr0);
-          hou0 = so * fmaf(beta, l31 ? ph.y : ph.x, ro);
-        } else {
-          p0[0] = p0[1] = p0[2] = p0[3] = 0.f;
-          hp0 = 0.f;
-          hou0 = 0.f;
+      float *S0 = cg3_smem + sidx * STAGE;
+      // ---- A: plane z_j, row y: p in place, own u kept
+      uBp = uB;
+      uB = uA;
+      hBp = hB0;
+      hB0 = hA0;
+      if (!INIT) {
+        const float4 r4 = ld4(S0 + rw + c), p4 = ld4(S0 + PLANE + rw + c);
+        const float4 s4 = ld4(S0 + 2 * PLANE + rw + c);
+        const float4 pn = make_float4(fmaf(beta, p4.x, r4.x), fmaf(beta, p4.y, r4.y),
+                                      fmaf(beta, p4.z, r4.z), fmaf(beta, p4.w, r4.w));
+        *reinterpret_cast<float4 *>(S0 + PLANE + rw + c) = pn;
+        uA = mul4(s4, pn);
+        if (l0 || l31) {
+          const float2 r2 = *reinterpret_cast<const float2 *>(S0 + rw + hA);
+          const float2 p2 = *reinterpret_cast<const float2 *>(S0 + PLANE + rw + hA);
+          const float2 s2 = *reinterpret_cast<const float2 *>(S0 + 2 * PLANE + rw + hA);
+          const float b0 = fmaf(beta, p2.x, r2.x), b1 = fmaf(beta, p2.y, r2.y);
+          *reinterpret_cast<float2 *>(S0 + PLANE + rw + hA) = make_float2(b0, b1);
+          hA0 = l31 ? s2.x * b0 : s2.y * b1;   // u of the column x0 + 128 / x0 - 1
         }
-        hu0 = hs0 * hp0;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) u0[c] = s0[c] * p0[c];
-        if (!INIT) {
-          float *U = ring_u + (j & 1) * PLANE + w * kWin;
-          *reinterpret_cast<float4 *>(U + 4 + 4 * lane) = make_float4(u0[0], u0[1], u0[2], u0[3]);
-          if (lane == 0 || l31) U[l31 ? kW + 4 : 3] = hu0;
-        }
-        const int lay = min(max(z, 0), g.nz - 1) >> cg.lgB;
-        if (lay != lay_A) {
-          lay_A = lay;
-          kA = cell_k(cg, kx, cxo, y, z, g);
-          hA = cell_k(cg, kx, cxh, y, z, g);
-        }
-        K0 = kA;
-        H0 = hA;
-        if (!INIT && doC && row_ok && j >= 2 && j < zc + 2 && z < g.nz && xl < px) {
-          const int64_t o = ((int64_t)z * g.ny + y) * px + xl;
-          dq0 = *reinterpret_cast<const float4 *>(d + o);
-          if (check) xq0 = __ldg(reinterpret_cast<const float4 *>(xref + o));
-        }
+      }
+      // d (and xref) of an output plane, for stage C two steps on
+      if (!INIT && doC && row_ok && j >= 2 && j < zc + 2 && z < g.nz && xl < px) {
+        const int64_t o = ((int64_t)z * g.ny + y) * px + xl;
+        dq0 = ld4(d + o);
+        if (check) xq0 = __ldg(reinterpret_cast<const float4 *>(xref + o));
       }
       // ---- B: plane z_{j-1}
       if (j >= 2 && doB) {
         const int z1 = z - dir;
-        const int lay = min(max(z1, 0), g.nz - 1) >> cg.lgB;
-        if (lay != lay_B) {
-          lay_B = lay;
-          const int kc = cell_k(cg, kx, cxo, y, z1, g), kh = cell_k(cg, kx, cxh, y, z1, g);
-          bL = p2f(kc - cell_k(cg, kx, cxl, y, z1, g));
-          bR = p2f(kc - cell_k(cg, kx, cxr, y, z1, g));
-          bS = p2f(kc - cell_k(cg, kx, cxo, y - 1, z1, g));
-          bN = p2f(kc - cell_k(cg, kx, cxo, y + 1, z1, g));
-          bxh = p2f(kh - kc);
-          bhS = p2f(kh - cell_k(cg, kx, cxh, y - 1, z1, g));
-          bhN = p2f(kh - cell_k(cg, kx, cxh, y + 1, z1, g));
-        }
+        const float *S1 = cg3_smem + ((q - 1) % NS) * STAGE;   // plane z1
+        float *RN = ring_n + ((q - 1) % 3) * PLANE;
+        float *RC = ring_c + ((q - 1) & 1) * 3 * PLANE;
+        const float4 r4 = ld4(S1 + rw + c), s4 = ld4(S1 + 2 * PLANE + rw + c);
+        float rn[4];
+        const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
+        float hrn = S1[rw + hB];
+        const float hs = S1[2 * PLANE + rw + hB];
         if (INIT) {
-#pragma unroll
-          for (int c = 0; c < 4; ++c) rn1[c] = r1[c];
-          hun1 = hs1 * hr1;
+          rn[0] = r4.x; rn[1] = r4.y; rn[2] = r4.z; rn[3] = r4.w;
         } else {
-          const float hz1 = (half && (z1 == 0 || z1 == g.nz - 1)) ? 0.5f : 1.f;
-          const float fP = p2f(K1 - K2), fN = p2f(K1 - K0);
-          const float *Us = ring_u + ((j - 1) & 1) * PLANE + (w - 1) * kWin;
-          const float *Un = Us + 2 * kWin;
-          const float4 us = *reinterpret_cast<const float4 *>(Us + 4 + 4 * lane);
-          const float4 un = *reinterpret_cast<const float4 *>(Un + 4 + 4 * lane);
-          const float ysv[4] = {us.x, us.y, us.z, us.w}, ynv[4] = {un.x, un.y, un.z, un.w};
-          float uL = __shfl_up_sync(0xffffffffu, u1[3], 1);
-          float uR = __shfl_down_sync(0xffffffffu, u1[0], 1);
-          if (lane == 0) uL = hu1;
-          if (l31) uR = hu1;
-          const float xs[4] = {fmaf(uL, bL, u1[1]), u1[0] + u1[2], u1[1] + u1[3],
-                               fmaf(uR, bR, u1[2])};
-          const float wxe = hy * hz1;
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const float ys = fmaf(ysv[c], bS, ynv[c] * bN);
-            const float zs = fmaf(u2[c], fP, u0[c] * fN);
-            const float acc = fmaf(wxe, xs[c], hx[c] * fmaf(hz1, ys, hy * zs));
-            const float sv = fmaf(-s1[c], acc, p1[c]);
-            rn1[c] = fmaf(-alpha, sv, r1[c]);
+          const int lay = min(max(z1, 0), g.nz - 1) >> cg.lgB;
+          const int layp = min(max(z1 - dir, 0), g.nz - 1) >> cg.lgB;
+          const int layn = min(max(z1 + dir, 0), g.nz - 1) >> cg.lgB;
+          if (lay != layB || layp != lay || layn != lay) {
+            // x / y factors change with the layer, z factors only next to
+            // another layer (uniform across the block)
+            layB = (layp != lay || layn != lay) ? INT_MIN : lay;
+            const int kc = cell_k(cg, kx, cxo, y, z1, g), kh = cell_k(cg, kx, cxh, y, z1, g);
+            bL = p2f(kc - cell_k(cg, kx, cxl, y, z1, g));
+            bR = p2f(kc - cell_k(cg, kx, cxr, y, z1, g));
+            bS = p2f(kc - cell_k(cg, kx, cxo, y - 1, z1, g));
+            bN = p2f(kc - cell_k(cg, kx, cxo, y + 1, z1, g));
+            bxh = p2f(kh - kc);
+            bhS = p2f(kh - cell_k(cg, kx, cxh, y - 1, z1, g));
+            bhN = p2f(kh - cell_k(cg, kx, cxh, y + 1, z1, g));
+            bP = p2f(kc - cell_k(cg, kx, cxo, y, z1 - dir, g));
+            bNz = p2f(kc - cell_k(cg, kx, cxo, y, z1 + dir, g));
+            bhP = p2f(kh - cell_k(cg, kx, cxh, y, z1 - dir, g));
+            bhNz = p2f(kh - cell_k(cg, kx, cxh, y, z1 + dir, g));
           }
-          // halo column
-          const float hyS = Us[l31 ? kW + 4 : 3], hyN = Un[l31 ? kW + 4 : 3];
-          const float uadj = l31 ? u1[3] : u1[0];
-          const float fPh = p2f(H1 - H2), fNh = p2f(H1 - H0);
-          const float acc = fmaf(wxe, fmaf(uadj, bxh, hou1),
-                                 hxh * fmaf(hz1, fmaf(hyS, bhS, hyN * bhN),
-                                            hy * fmaf(hu2, fPh, hu0 * fNh)));
-          hun1 = hs1 * fmaf(-alpha, fmaf(-hs1, acc, hp1), hr1);
-        }
+          const float hz1 = (half && (z1 == 0 || z1 == g.nz - 1)) ? 0.5f : 1.f;
+          const float wxe = hy * hz1;
+          const float4 p4 = ld4(S1 + PLANE + rw + c);
+          const float4 uc = uB;
+          const float uL = S1[2 * PLANE + rw + c - 1] * S1[PLANE + rw + c - 1];
+          const float uR = S1[2 * PLANE + rw + c + 4] * S1[PLANE + rw + c + 4];
+          const float4 us = mul4(ld4(S1 + 2 * PLANE + rw - kWin + c), ld4(S1 + PLANE + rw - kWin + c));
+          const float4 un = mul4(ld4(S1 + 2 * PLANE + rw + kWin + c), ld4(S1 + PLANE + rw + kWin + c));
+          const float xs[4] = {fmaf(uL, bL, uc.y), uc.x + uc.z, uc.y + uc.w, fmaf(uR, bR, uc.z)};
+          const float ysS[4] = {us.x, us.y, us.z, us.w}, ysN[4] = {un.x, un.y, un.z, un.w};
+          const float zsP[4] = {uBp.x, uBp.y, uBp.z, uBp.w}, zsN[4] = {uA.x, uA.y, uA.z, uA.w};
+          const float pv[4] = {p4.x, p4.y, p4.z, p4.w}, rv[4] = {r4.x, r4.y, r4.z, r4.w};
 #pragma unroll
-        for (int c = 0; c < 4; ++c) un1[c] = s1[c] * rn1[c];
-        float *N = ring_n + ((j - 1) & 1) * PLANE + w * kWin;
-        *reinterpret_cast<float4 *>(N + 4 + 4 * lane) = make_float4(un1[0], un1[1], un1[2], un1[3]);
-        if (lane == 0 || l31) N[l31 ? kW + 4 : 3] = hun1;
+          for (int i = 0; i < 4; ++i) {
+            const float ys = fmaf(ysS[i], bS, ysN[i] * bN);
+            const float zs = fmaf(zsP[i], bP, zsN[i] * bNz);
+            const float acc = fmaf(wxe, xs[i], hx[i] * fmaf(hz1, ys, hy * zs));
+            rn[i] = fmaf(-alpha, fmaf(-sv[i], acc, pv[i]), rv[i]);
+          }
+          if (l0 || l31) {
+            const float uin = S1[2 * PLANE + rw + hI] * S1[PLANE + rw + hI];
+            const float uout = S1[2 * PLANE + rw + hO] * S1[PLANE + rw + hO];
+            const float uS = S1[2 * PLANE + rw - kWin + hB] * S1[PLANE + rw - kWin + hB];
+            const float uN = S1[2 * PLANE + rw + kWin + hB] * S1[PLANE + rw + kWin + hB];
+            const float acc =
+                fmaf(wxe, fmaf(uin, bxh, uout),
+                     hxh * fmaf(hz1, fmaf(uS, bhS, uN * bhN), hy * fmaf(hBp, bhP, hA0 * bhNz)));
+            hrn = fmaf(-alpha, fmaf(-hs, acc, S1[PLANE + rw + hB]), hrn);
+          }
+        }
+        st4(RN + rw + c, sv[0] * rn[0], sv[1] * rn[1], sv[2] * rn[2], sv[3] * rn[3]);
+        if (l0 || l31) RN[rw + hB] = hs * hrn;
+        if (doC) {   // C reads r_new, sig and p of this plane one step on
+          st4(RC + rw + c, rn[0], rn[1], rn[2], rn[3]);
+          *reinterpret_cast<float4 *>(RC + PLANE + rw + c) = s4;
+          if (!INIT) *reinterpret_cast<float4 *>(RC + 2 * PLANE + rw + c) = ld4(S1 + PLANE + rw + c);
+        }
       }
-      // ---- C: plane z_{j-2}
+      // ---- C: plane z_{j-2} (B wrote its neighbours' un in earlier steps,
+      // and this warp's own un of plane z_{j-1} just now)
       if (j >= 4 && doC) {
         const int z2 = z - 2 * dir;
         if (z2 < g.nz && row_ok) {
           const int lay = z2 >> cg.lgB;
-          if (lay != lay_C) {
-            lay_C = lay;
+          const int layp = min(max(z2 - dir, 0), g.nz - 1) >> cg.lgB;
+          const int layn = min(max(z2 + dir, 0), g.nz - 1) >> cg.lgB;
+          if (lay != layC || layp != lay || layn != lay) {
+            layC = (layp != lay || layn != lay) ? INT_MIN : lay;
             const int kc = cell_k(cg, kx, cxo, y, z2, g);
             cL = p2f(kc - cell_k(cg, kx, cxl, y, z2, g));
             cR = p2f(kc - cell_k(cg, kx, cxr, y, z2, g));
             cS = p2f(kc - cell_k(cg, kx, cxo, y - 1, z2, g));
             cN = p2f(kc - cell_k(cg, kx, cxo, y + 1, z2, g));
+            cP = p2f(kc - cell_k(cg, kx, cxo, y, z2 - dir, g));
+            cNz = p2f(kc - cell_k(cg, kx, cxo, y, z2 + dir, g));
             cW = p2f(-2 * kc - fd);
           }
           const float hz2 = (half && (z2 == 0 || z2 == g.nz - 1)) ? 0.5f : 1.f;
-          const float fP = p2f(K2 - K3), fN = p2f(K2 - K1);
-          const float *Ns = ring_n + ((j - 2) & 1) * PLANE + (w - 1) * kWin;
-          const float *Nn = Ns + 2 * kWin;
-          const float4 ns = *reinterpret_cast<const float4 *>(Ns + 4 + 4 * lane);
-          const float4 nn = *reinterpret_cast<const float4 *>(Nn + 4 + 4 * lane);
-          const float ysv[4] = {ns.x, ns.y, ns.z, ns.w}, ynv[4] = {nn.x, nn.y, nn.z, nn.w};
-          float uL = __shfl_up_sync(0xffffffffu, un2[3], 1);
-          float uR = __shfl_down_sync(0xffffffffu, un2[0], 1);
-          if (lane == 0) uL = hun2;
-          if (l31) uR = hun2;
-          const float xs[4] = {fmaf(uL, cL, un2[1]), un2[0] + un2[2], un2[1] + un2[3],
-                               fmaf(uR, cR, un2[2])};
           const float wxe = hy * hz2;
+          const float *RC = ring_c + ((q - 2) & 1) * 3 * PLANE;   // plane z2: r_new, sig, p
+          const float *Nc = ring_n + ((q - 2) % 3) * PLANE;       // un of plane z2
+          const float *Np = ring_n + ((q - 3) % 3) * PLANE;       // plane z2 - dir
+          const float *Nn = ring_n + ((q - 1) % 3) * PLANE;       // plane z2 + dir
+          const float4 nc = ld4(Nc + rw + c);
+          const float nL = Nc[rw + c - 1], nR = Nc[rw + c + 4];
+          const float4 ns = ld4(Nc + rw - kWin + c), nn = ld4(Nc + rw + kWin + c);
+          const float4 np = ld4(Np + rw + c), nz = ld4(Nn + rw + c);
+          const float4 rn4 = ld4(RC + rw + c), s4 = ld4(RC + PLANE + rw + c);
+          const float xs[4] = {fmaf(nL, cL, nc.y), nc.x + nc.z, nc.y + nc.w, fmaf(nR, cR, nc.z)};
+          const float ysS[4] = {ns.x, ns.y, ns.z, ns.w}, ysN[4] = {nn.x, nn.y, nn.z, nn.w};
+          const float zsP[4] = {np.x, np.y, np.z, np.w}, zsN[4] = {nz.x, nz.y, nz.z, nz.w};
+          const float rv[4] = {rn4.x, rn4.y, rn4.z, rn4.w}, sv[4] = {s4.x, s4.y, s4.z, s4.w};
+          float pv[4] = {0, 0, 0, 0};
+          if (!INIT) {
+            const float4 p4 = ld4(RC + 2 * PLANE + rw + c);
+            pv[0] = p4.x; pv[1] = p4.y; pv[2] = p4.z; pv[3] = p4.w;
+          }
           const float dv[4] = {dq2.x, dq2.y, dq2.z, dq2.w};
           const float xv[4] = {xq2.x, xq2.y, xq2.z, xq2.w};
-          float dn[4], ro[4], po[4];
+          float dn[4];
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const float ys = fmaf(ysv[c], cS, ynv[c] * cN);
-            const float zs = fmaf(un3[c], fP, un1[c] * fN);
-            const float acc = fmaf(wxe, xs[c], hx[c] * fmaf(hz2, ys, hy * zs));
-            const float wv = fmaf(-s2[c], acc, rn2[c]);
-            const float tt = rn2[c] * cW;
-            gam = fmaf(tt, rn2[c], gam);
+          for (int i = 0; i < 4; ++i) {
+            const float ys = fmaf(ysS[i], cS, ysN[i] * cN);
+            const float zs = fmaf(zsP[i], cP, zsN[i] * cNz);
+            const float acc = fmaf(wxe, xs[i], hx[i] * fmaf(hz2, ys, hy * zs));
+            const float wv = fmaf(-sv[i], acc, rv[i]);
+            const float tt = rv[i] * cW;
+            gam = fmaf(tt, rv[i], gam);
             dlt = fmaf(tt, wv, dlt);
-            rmax = fmaxf(rmax, fabsf(rn2[c]));
-            if (!INIT) {
-              dn[c] = fmaf(alphaF, p2[c], dv[c]);
-              pmax = fmaxf(pmax, fabsf(p2[c]));
-              ro[c] = rn2[c] * gwr;
-              po[c] = p2[c] * gwr;
-              if (check && fabsf(rn2[c]) > thetaF * fabsf(xv[c] + dn[c])) bad = 1;
-            }
+            rmax = fmaxf(rmax, fabsf(rv[i]));
+            dn[i] = fmaf(alphaF, pv[i], dv[i]);
+            pmax = fmaxf(pmax, fabsf(pv[i]));
+            if (check && fabsf(rv[i]) > thetaF * fabsf(xv[i] + dn[i])) bad = 1;
           }
           if (!INIT && st_ok) {
             const int64_t o = ((int64_t)z2 * g.ny + y) * px + xl;
-            *reinterpret_cast<float4 *>(d + o) = make_float4(dn[0], dn[1], dn[2], dn[3]);
-            *reinterpret_cast<float4 *>(r_out + o) = make_float4(ro[0], ro[1], ro[2], ro[3]);
-            *reinterpret_cast<float4 *>(p_out + o) = make_float4(po[0], po[1], po[2], po[3]);
+            st4(d + o, dn[0], dn[1], dn[2], dn[3]);
+            st4(r_out + o, rv[0] * gwr, rv[1] * gwr, rv[2] * gwr, rv[3] * gwr);
+            st4(p_out + o, pv[0] * gwr, pv[1] * gwr, pv[2] * gwr, pv[3] * gwr);
           }
         }
-      }
-      // every warp is done with this plane's stage and with the ring slots
-      // the next step overwrites
-      __syncthreads();
-      if (threadIdx.x == 0 && next_issue < nq) {
-        fence_proxy_async();
-        issue(next_issue);
-        ++next_issue;
-      }
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        un3[c] = un2[c];
-        un2[c] = un1[c];
-        rn2[c] = rn1[c];
-        p2[c] = p1[c];
-        s2[c] = s1[c];
-        u2[c] = u1[c];
-        r1[c] = r0[c];
-        p1[c] = p0[c];
-        s1[c] = s0[c];
-        u1[c] = u0[c];
       }
       dq2 = dq1;
       dq1 = dq0;
       xq2 = xq1;
       xq1 = xq0;
-      hun2 = hun1;
-      hu2 = hu1;
-      hr1 = hr0;
-      hp1 = hp0;
-      hs1 = hs0;
-      hu1 = hu0;
-      hou1 = hou0;
-      K3 = K2;
-      K2 = K1;
-      K1 = K0;
-      H2 = H1;
-      H1 = H0;
+      // every warp is done with the stage of the plane of one step ago and
+      // with the ring slots the next step overwrites
+      __syncthreads();
+      if (threadIdx.x == 0 && q >= 1 && next_issue < nq) {
+        fence_proxy_async();
+        issue(next_issue);
+        ++next_issue;
+      }
     }
   }
   if (fault) {
@@ -1000,11 +982,12 @@ bool plan2d(Cg32Plan *pl, const Grid &g, int num_sms) {
   }
 }
 
-// 3D variants: (rows per tile TY, stages NS); smem: NS stages of three
-// arrays plus the two rings, each (TY + 4) rows of 136 floats
+// 3D variants: (rows per tile TY, stages NS); shared memory: NS stages of
+// three planes, a ring of three un planes and one of two (r_new, sig, p)
+// planes, each (TY + 4) rows of 136 floats
 template <int TY, int NS>
 size_t smem3d() {
-  return (size_t)(3 * NS + 4) * (TY + 4) * kWin * sizeof(float) + 128;
+  return (size_t)(3 * NS + 3 + 6) * (TY + 4) * kWin * sizeof(float) + 128;
 }
 
 template <int TY, int NS>
@@ -1061,24 +1044,24 @@ void launch3d_t(const Cg32Plan &pl, const Grid &g, const CellGrid &cg, const Cg3
       b.r[o], b.p[o], b.d, b.xref, b.st, b.part, b.nblk_part, b.px);
 }
 
-// 3D variant table: 1 = (TY 8, 4 stages), 2 = (12, 4), 3 = (4, 4), 4 = (8, 3)
+// 3D variant table (TY, stages): 1 = (12, 5), 2 = (8, 6), 3 = (16, 4), 4 = (8, 8)
 template <bool INIT>
 void launch3d(const Cg32Plan &pl, const Grid &g, const CellGrid &cg, const Cg32Buffers &b,
               int set, cudaStream_t s) {
   switch (pl.variant) {
-    case 2: launch3d_t<INIT, 12, 4>(pl, g, cg, b, set, s); break;
-    case 3: launch3d_t<INIT, 4, 4>(pl, g, cg, b, set, s); break;
-    case 4: launch3d_t<INIT, 8, 3>(pl, g, cg, b, set, s); break;
-    default: launch3d_t<INIT, 8, 4>(pl, g, cg, b, set, s); break;
+    case 2: launch3d_t<INIT, 8, 6>(pl, g, cg, b, set, s); break;
+    case 3: launch3d_t<INIT, 16, 4>(pl, g, cg, b, set, s); break;
+    case 4: launch3d_t<INIT, 8, 8>(pl, g, cg, b, set, s); break;
+    default: launch3d_t<INIT, 12, 5>(pl, g, cg, b, set, s); break;
   }
 }
 
 bool plan3d(Cg32Plan *pl, const Grid &g, int num_sms) {
   switch (pl->variant) {
-    case 2: return plan3d_t<12, 4>(pl, g, num_sms);
-    case 3: return plan3d_t<4, 4>(pl, g, num_sms);
-    case 4: return plan3d_t<8, 3>(pl, g, num_sms);
-    default: pl->variant = 1; return plan3d_t<8, 4>(pl, g, num_sms);
+    case 2: return plan3d_t<8, 6>(pl, g, num_sms);
+    case 3: return plan3d_t<16, 4>(pl, g, num_sms);
+    case 4: return plan3d_t<8, 8>(pl, g, num_sms);
+    default: pl->variant = 1; return plan3d_t<12, 5>(pl, g, num_sms);
   }
 }
 
