@@ -92,6 +92,11 @@ def parse():
     ap.add_argument("--modes", default="both", choices=["both", "one"],
                     help="single-grid workloads: time both precision modes (default) or only "
                          "--precision (shorter profiler captures)")
+    ap.add_argument("--batch-pack", type=int, default=0, choices=[-1, 0, 1],
+                    help="batched workload: 0/1 packed (one launch per pass over all "
+                         "instances), -1 each instance on its own stream")
+    ap.add_argument("--batch-tile-rows", type=int, default=0,
+                    help="packed batches: rows per tile (0 = autotuned)")
     ap.add_argument("--no-c3-block", action="store_true",
                     help="default 2D workload: skip timing the 3D 256^3 workload beside it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -508,13 +513,15 @@ def run_batch(args):
     n_unk = [i.n - len(np.unique(i.src_idx)) for i in insts]
     opt = eik.make_options(precision=args.precision, tol=args.tol,
                            tile_override=args.tile_override, band_bits=args.band_bits,
-                           inner_tol=args.inner_tol)
+                           inner_tol=args.inner_tol, batch_pack=args.batch_pack,
+                           batch_tile_rows=args.batch_tile_rows)
     b = eik.eik_create_batch(insts, opt, workers=args.workers)
     S = torch.empty(b.n, dtype=torch.float64, device="cuda")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
         eik.eik_solve_batch(b, S_out=S)
     times, units = [], 0
+    info0 = eik.eik_batch_info(b)
     with Clocks(local) as clk:
         for _ in range(args.steps):
             flush_l2(flush)
@@ -527,7 +534,26 @@ def run_batch(args):
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1) / 1e3)
             units += sum(u * st["inner_iters"] for u, st in zip(n_unk, stats))
+    info1 = eik.eik_batch_info(b)
     total, units = job_totals(sum(times), units, ws, "cuda")
+    roof = None
+    if info1["packed"] and info1["pass_ms"] > info0["pass_ms"]:
+        # the packed pass: 28 B per covered node (the single-grid pass's 7
+        # words) over the device time of the graphs that ran the passes
+        peak, peak_src = measured_peaks()
+        work = info1["node_passes"] - info0["node_passes"]
+        sec = (info1["pass_ms"] - info0["pass_ms"]) * 1e-3
+        npass = info1["passes"] - info0["passes"]
+        achieved = ALGO_BYTES_PER_NODE["mixed_cg"] * work / sec / 1e9
+        roof = {"bound": "hbm", "kernel": "mixed_cg_packed (k_cg2d_batch)",
+                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": round(ALGO_BYTES_PER_NODE["mixed_cg"] * work
+                                                      / max(npass, 1)),
+                "avg_launch_us": round(1e6 * sec / max(npass, 1), 2),
+                "passes": npass, "node_passes": work,
+                "share_of_step": round(sec / sum(times), 4)}
     if rank != 0:
         return
     line = {"metric": METRIC, "value": round(units / total / 1e9, 4), "unit": UNIT,
@@ -543,7 +569,9 @@ def run_batch(args):
                        "l2": "flushed between steps (256 MiB write)"},
             "clocks": clk.summary(),
             "iterations": {"min": min(s_["inner_iters"] for s_ in stats),
-                           "max": max(s_["inner_iters"] for s_ in stats)}}
+                           "max": max(s_["inner_iters"] for s_ in stats)},
+            "batch": {k: info1[k] for k in ("packed", "variant", "tile_rows", "tuned")},
+            "roofline": roof}
     eik.eik_destroy_batch(b)
     if rank == 0:
         print(json.dumps(line), flush=True)

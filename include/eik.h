@@ -116,7 +116,17 @@ typedef struct {
                          so its bounded wait (0.2 s) expires and the solve
                          returns EIK_ERR_TIMEOUT; exercises the timeout path
                          without any fault. */
-  int reserved[5];
+  int batch_pack;     /* eik_create_batch of 2D mixed-precision instances:
+                         0 (default) or 1 = packed: the instances share one
+                         set of FP32 inner-CG arrays and every inner-CG pass
+                         is one launch over a tile list spanning all of them
+                         (see eik_create_batch); -1 = each instance solves on
+                         its own stream.  Ignored for FP64 and 3D batches
+                         (always per-instance). */
+  int batch_tile_rows;/* packed batches: rows per tile of the packed pass
+                         (1..1024); 0 = autotuned.  tile_override (1..4)
+                         fixes the pass's 2D variant; 0 = autotuned. */
+  int reserved[3];
 } eik_options;
 
 typedef struct {
@@ -180,10 +190,26 @@ eik_status eik_grad(eik_handle *h, const double *dLdS, double *dLdf,
 
 /*
  * Batched solves: many independent instances (own grid, h, hbar, f and
- * sources; Sec. 6 system per instance) solved together.  Each instance runs
- * on its own internal stream with its own convergence test, so the GPU
- * executes the kernels of many instances concurrently; instances stop
- * independently.  All instances share ndim and the options.
+ * sources; Sec. 6 system per instance) solved together, each with its own
+ * refinement and convergence test; instances stop independently.  All
+ * instances share ndim and the options.
+ *
+ * Packed (2D mixed precision, the default there; eik_options.batch_pack):
+ * the FP32 inner-CG arrays of all instances are stacked in one pitched
+ * array, and an inner solve runs for every instance that needs one at once:
+ * each CG iteration is ONE kernel launch over a tile list spanning all those
+ * instances, with per-instance recurrence scalars and stopping tests, and an
+ * instance whose inner solve has ended leaves the list.  The iterations run
+ * as a captured CUDA graph.  The tile shape (kernel variant, rows per tile)
+ * is autotuned at the first solve: each candidate is timed on the batch's
+ * own geometry and the fastest is cached in a JSON file, keyed by GPU name,
+ * dimension, precision and size class (log2 of the node and instance
+ * counts); the file is $EIK_TUNE_CACHE if set ("" or "off": no file), else
+ * $XDG_CACHE_HOME/eik/tune.json or $HOME/.cache/eik/tune.json.  The FP64
+ * refinement steps of each instance run on its own stream, one host thread
+ * per instance.
+ * Per-instance (FP64, 3D, or batch_pack = -1): each instance runs on its own
+ * internal stream, and host worker threads drive them concurrently.
  *   count        number of instances (>= 1)
  *   dims         count*ndim extents, instance-major
  *   h, hbar      count values each
@@ -205,8 +231,23 @@ eik_status eik_set_f_batch(eik_batch *b, const double *f);
 eik_status eik_solve_batch(eik_batch *b, double *S_out, eik_stats *stats);
 eik_status eik_grad_batch(eik_batch *b, const double *dLdS, double *dLdf, eik_stats *stats);
 eik_status eik_destroy_batch(eik_batch *b);
-/* Instances solved concurrently (host worker threads); 0 = library choice. */
+/* Instances solved concurrently (host worker threads) in per-instance
+ * batches; 0 = library choice.  No effect on packed batches. */
 eik_status eik_batch_set_concurrency(eik_batch *b, int workers);
+/*
+ * How the batch runs: *packed = 1 for a packed batch, else 0; for a packed
+ * batch the pass's 2D variant (1..4), its rows per tile, and how they were
+ * chosen (*tuned: 0 fixed by the options, 1 measured by the autotuner, 2
+ * read from the cache file; all 0 before the first solve); *passes, the
+ * packed inner-CG launches that had work (the autotuner's included) since
+ * creation; and, over the solves only, *node_passes, the sum over passes of
+ * the grid nodes each covered (a pass moves 28 bytes per node), and
+ * *pass_ms, the device time of the CUDA graphs that ran them (CUDA events).
+ * Any output pointer may be NULL.
+ */
+eik_status eik_batch_info(const eik_batch *b, int *packed, int *variant, int *tile_rows,
+                          int *tuned, int64_t *passes, int64_t *node_passes,
+                          double *pass_ms);
 
 /*
  * Componentwise residual of a given S without allocating any device memory

@@ -40,7 +40,8 @@ class Options(ctypes.Structure):
                 ("boundary", ctypes.c_int), ("tile_override", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
                 ("band_bits", ctypes.c_int), ("test_flags", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("batch_pack", ctypes.c_int), ("batch_tile_rows", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
 
 
 class Stats(ctypes.Structure):
@@ -88,6 +89,11 @@ _SIGS = [
     ("eik_grad_batch", ctypes.c_int, [_P, _P, _P, _P]),
     ("eik_destroy_batch", ctypes.c_int, [_P]),
     ("eik_batch_set_concurrency", ctypes.c_int, [_P, ctypes.c_int]),
+    ("eik_batch_info", ctypes.c_int,
+     [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+      ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+      ctypes.POINTER(ctypes.c_double)]),
     ("eik_residual_noalloc", ctypes.c_int,
      [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_double, ctypes.c_double, _P, _P,
       _P, ctypes.c_int64, ctypes.c_int, _P, _P]),

@@ -13,6 +13,7 @@
 #include <string>
 #include <vector>
 
+#include "eik_batch.h"
 #include "eik_internal.cuh"
 #include "eik_launch.h"
 #include "eik_mixed.h"
@@ -394,10 +395,12 @@ int eik_cuda_arch(void) {
 #endif
 }
 
-eik_status eik_create(eik_handle **out, int ndim, const int64_t *dims, double hsp,
-                      double hbar, const double *f, const int64_t *src_idx,
-                      const double *src_U, int64_t nsrc, const eik_options *opt,
-                      eik_stream_t stream) {
+// Creates one solver; with exec, a member of a packed batch whose FP32
+// inner-CG arrays live in the batch's atlas (instance `member`).
+static eik_status create_impl(eik_handle **out, int ndim, const int64_t *dims, double hsp,
+                              double hbar, const double *f, const int64_t *src_idx,
+                              const double *src_U, int64_t nsrc, const eik_options *opt,
+                              eik_stream_t stream, BatchExec *exec, int member) {
   if (!out) return fail(EIK_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (ndim != 2 && ndim != 3) return fail(EIK_ERR_ARG, "ndim must be 2 or 3");
@@ -425,6 +428,10 @@ eik_status eik_create(eik_handle **out, int ndim, const int64_t *dims, double hs
   if (!(o.tol > 0) || o.max_iter < 1) return fail(EIK_ERR_ARG, "tol and max_iter must be > 0");
   if (o.tile_override < 0 || o.tile_override > 4)
     return fail(EIK_ERR_ARG, "tile_override must be in 0..4");
+  if (o.batch_pack < -1 || o.batch_pack > 1)
+    return fail(EIK_ERR_ARG, "batch_pack must be -1, 0 or 1");
+  if (o.batch_tile_rows < 0 || o.batch_tile_rows > 1024)
+    return fail(EIK_ERR_ARG, "batch_tile_rows must be in 0..1024");
 
   eik_handle *h = new (std::nothrow) eik_handle();
   if (!h) return fail(EIK_ERR_OOM, "host allocation failed");
@@ -528,7 +535,10 @@ eik_status eik_create(eik_handle **out, int ndim, const int64_t *dims, double hs
                        h->stream));
     CK(cudaStreamSynchronize(h->stream));
     if (o.precision == EIK_PREC_MIXED) {
-      eik_status ms = mixed_create(&h->mixed, g, h->tc, h->num_sms, o.tile_override, h->stream);
+      eik_status ms = exec ? mixed_create_member(&h->mixed, g, h->tc, h->num_sms, exec, member,
+                                                 h->stream)
+                           : mixed_create(&h->mixed, g, h->tc, h->num_sms, o.tile_override,
+                                          h->stream);
       if (ms != EIK_OK) {
         free_handle(h);
         return fail(ms, "mixed-precision workspace allocation failed");
@@ -550,6 +560,14 @@ eik_status eik_create(eik_handle **out, int ndim, const int64_t *dims, double hs
   }
   *out = h;
   return EIK_OK;
+}
+
+eik_status eik_create(eik_handle **out, int ndim, const int64_t *dims, double hsp,
+                      double hbar, const double *f, const int64_t *src_idx,
+                      const double *src_U, int64_t nsrc, const eik_options *opt,
+                      eik_stream_t stream) {
+  return create_impl(out, ndim, dims, hsp, hbar, f, src_idx, src_U, nsrc, opt, stream, nullptr,
+                     -1);
 }
 
 eik_status eik_set_f(eik_handle *h, const double *f) {
@@ -756,6 +774,7 @@ struct eik_batch {
   int workers = 0;
   std::vector<eik_handle *> hs;
   std::vector<int64_t> off;   // node offsets, count+1
+  BatchExec *exec = nullptr;  // packed 2D mixed batches
 };
 
 namespace {
@@ -828,11 +847,41 @@ eik_status eik_create_batch(eik_batch **out, int count, int ndim, const int64_t 
       return fail(EIK_ERR_ARG, "src_offsets must be non-decreasing");
     }
   }
+  eik_options o;
+  eik_default_options(&o);
+  if (opt) o = *opt;
+  if (ndim == 2 && o.precision == EIK_PREC_MIXED && o.batch_pack >= 0) {
+    // packed: one atlas for the FP32 arrays of every instance
+    std::vector<int> nx(count), ny(count);
+    for (int i = 0; i < count; ++i) {
+      const int64_t ex = dims[2 * (int64_t)i], ey = dims[2 * (int64_t)i + 1];
+      if (ex < 2 || ey < 2 || ex > (1 << 20) || ey > (1 << 20)) {
+        delete b;
+        return fail(EIK_ERR_ARG, "packed batch: each extent must be in 2 .. 2^20");
+      }
+      nx[i] = (int)ex;
+      ny[i] = (int)ey;
+    }
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (o.tile_override < 0 || o.tile_override > 4 || o.batch_tile_rows < 0 ||
+        o.batch_tile_rows > 1024) {
+      delete b;
+      return fail(EIK_ERR_ARG, "invalid tile_override or batch_tile_rows");
+    }
+    const eik_status es = batch_exec_create(&b->exec, count, nx.data(), ny.data(), o.boundary,
+                                            nsm, o.tile_override, o.batch_tile_rows);
+    if (es != EIK_OK) {
+      delete b;
+      return fail(es, "packed batch: atlas allocation failed");
+    }
+  }
   b->hs.assign(count, nullptr);
   for (int i = 0; i < count; ++i) {
-    eik_status st = eik_create(&b->hs[i], ndim, dims + (int64_t)i * ndim, h[i], hbar[i],
-                               f + b->off[i], src_idx + so[i], src_U ? src_U + so[i] : nullptr,
-                               so[i + 1] - so[i], opt, stream);
+    eik_status st = create_impl(&b->hs[i], ndim, dims + (int64_t)i * ndim, h[i], hbar[i],
+                                f + b->off[i], src_idx + so[i], src_U ? src_U + so[i] : nullptr,
+                                so[i + 1] - so[i], opt, stream, b->exec, i);
     if (st != EIK_OK) {
       const std::string m = "instance " + std::to_string(i) + ": " + g_last_error;
       eik_destroy_batch(b);
@@ -856,9 +905,57 @@ eik_status eik_set_f_batch(eik_batch *b, const double *f) {
 
 eik_status eik_solve_batch(eik_batch *b, double *S_out, eik_stats *stats) {
   if (!b || !S_out) return fail(EIK_ERR_ARG, "NULL batch or S_out");
-  return run_pool(b, [&](int i) {
-    return eik_solve(b->hs[i], S_out + b->off[i], nullptr, stats ? stats + i : nullptr);
-  });
+  if (!b->exec)
+    return run_pool(b, [&](int i) {
+      return eik_solve(b->hs[i], S_out + b->off[i], nullptr, stats ? stats + i : nullptr);
+    });
+  // packed: every instance's program on its own host thread; their inner
+  // solves meet in the batch executor
+  const eik_status bs = batch_exec_begin(b->exec, b->count);
+  if (bs != EIK_OK) return fail(bs, "packed batch: " + batch_exec_error(b->exec));
+  const int n = b->count;
+  std::vector<eik_status> st(n, EIK_OK);
+  std::vector<std::string> msg(n);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::vector<std::thread> th;
+  th.reserve(n);
+  for (int i = 0; i < n; ++i)
+    th.emplace_back([&, i]() {
+      cudaSetDevice(dev);
+      st[i] = eik_solve(b->hs[i], S_out + b->off[i], nullptr, stats ? stats + i : nullptr);
+      if (st[i] != EIK_OK) msg[i] = eik_last_error();
+      batch_exec_leave(b->exec, i);
+    });
+  for (auto &t : th) t.join();
+  const eik_status es = batch_exec_end(b->exec);
+  for (int i = 0; i < n; ++i)
+    if (st[i] != EIK_OK) {
+      g_last_error = "instance " + std::to_string(i) + ": " + msg[i];
+      return st[i];
+    }
+  if (es != EIK_OK) return fail(es, "packed batch: " + batch_exec_error(b->exec));
+  return EIK_OK;
+}
+
+eik_status eik_batch_info(const eik_batch *b, int *packed, int *variant, int *tile_rows,
+                          int *tuned, int64_t *passes, int64_t *node_passes, double *pass_ms) {
+  if (!b) return fail(EIK_ERR_ARG, "NULL batch");
+  int v = 0, ty = 0, how = 0;
+  int64_t work = 0;
+  double ms = 0.0;
+  if (b->exec) {
+    batch_exec_plan(b->exec, &v, &ty, &how);
+    batch_exec_work(b->exec, &work, &ms);
+  }
+  if (packed) *packed = b->exec ? 1 : 0;
+  if (variant) *variant = v;
+  if (tile_rows) *tile_rows = ty;
+  if (tuned) *tuned = how;
+  if (passes) *passes = b->exec ? batch_exec_passes(b->exec) : 0;
+  if (node_passes) *node_passes = work;
+  if (pass_ms) *pass_ms = ms;
+  return EIK_OK;
 }
 
 eik_status eik_grad_batch(eik_batch *b, const double *dLdS, double *dLdf, eik_stats *stats) {
@@ -872,6 +969,7 @@ eik_status eik_destroy_batch(eik_batch *b) {
   if (!b) return EIK_OK;
   for (eik_handle *h : b->hs)
     if (h) free_handle(h);
+  batch_exec_destroy(b->exec);   // after the members, whose arrays it holds
   delete b;
   return EIK_OK;
 }

@@ -45,6 +45,9 @@ __device__ __forceinline__ double acc_ratio(const Acc &a, const Acc &b) {
 }
 
 // --------------------------------------------------------------- pass tail
+__device__ void cg_update(MixCtl *st, double G, double D, double R, double P, double Bd,
+                          bool INIT);
+
 // Per-block partials: <r,r> and <w,r> (both in units of 2^(2F + fd)), the
 // largest |r| and |p| (frame units), and the componentwise-test flag.  The
 // last block forms the next alpha, beta, frame and the stopping decision.
@@ -132,6 +135,15 @@ __device__ void cg_tail(float gam, float dlt, float rmax, float pmax, int bad, b
     Bd = fmax(Bd, tb[k]);
   }
   st->counter[1] = 0u;
+  cg_update(st, G, D, R, P, Bd, INIT);
+}
+
+// The recurrence step of one inner solve from the pass's totals: G = <r,r>,
+// D = <w,r> (units 2^(2F + fd)), R = max|r|, P = max|p| (frame units), Bd the
+// componentwise-test flag.  INIT: the solve's first pass (w = A r).  Run by
+// one thread.
+__device__ void cg_update(MixCtl *st, double G, double D, double R, double P, double Bd,
+                          bool INIT) {
   const int F = st->F, dF = st->dF, fd = st->fd;
   const Acc gam_new = acc_of(G, 2 * F + fd);
   const Acc dlt_new = acc_of(D, 2 * F + fd);
@@ -542,6 +554,472 @@ k_cg2d(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtenso
   }
   __syncwarp();
   cg_tail<INIT>(gam, dlt, rmax, pmax, bad, fault, st, part, nblk_part);
+}
+
+// ------------------------------------------------------- packed 2D batch
+// The 2D pass over a tile list spanning many instances of one atlas (BInst).
+// List position t is a tile of act[a] (pre[a] <= t < pre[a + 1]); warp gw
+// runs positions gw, gw + nw, ... as one pipeline, exactly as k_cg2d runs its
+// tiles, with the tile's instance data and recurrence scalars read at the
+// tile's start.  Instances join and leave the list between passes, each at
+// its own pace:
+//   * a tile's dots go to its own partial slot; the warp that completes an
+//     instance's last tile of the pass combines that instance's slots in
+//     list order and advances its recurrence (cg_update), and when the inner
+//     solve has ended it writes the outcome to the instance's host record;
+//   * the last warp of the pass drops the instances that ended and admits
+//     the requests waiting in the host ring, for the next pass.
+// An instance's first pass (MixCtl.first, with alpha = beta = 0 and p = 0)
+// computes w = A r and the dots, and writes r as both r and p of the other
+// buffer set, which is what its second pass expects (p = r + 0 p).  Each
+// instance reads buffer set (launch set ^ flip), flip fixed on admission so
+// that its first pass reads set 0, where the FP64 residual kernel put r.
+
+__device__ __forceinline__ int ld_acquire_sys(const volatile int *p) {
+  int v;
+  asm volatile("ld.acquire.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ int batch_find(const int *pre, int m, int t) {
+  int lo = 0, hi = m;   // pre[lo] <= t < pre[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (pre[mid] <= t)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// End of one tile: its partials, and the instance's recurrence step when this
+// was the instance's last tile of the pass.  Whole warp.
+__device__ void batch_tile_done(float gam, float dlt, float rmax, float pmax, int bad, int t,
+                                int inst, int a, const int *pre, MixCtl *st, unsigned *cnt,
+                                int *alive, BatchCtl *bc, double *part, int cap,
+                                BatchDone *done) {
+  const int lane = threadIdx.x & 31;
+  for (int o = 16; o > 0; o >>= 1) {
+    gam += __shfl_down_sync(0xffffffffu, gam, o);
+    dlt += __shfl_down_sync(0xffffffffu, dlt, o);
+    rmax = fmaxf(rmax, __shfl_down_sync(0xffffffffu, rmax, o));
+    pmax = fmaxf(pmax, __shfl_down_sync(0xffffffffu, pmax, o));
+    bad |= __shfl_down_sync(0xffffffffu, bad, o);
+  }
+  const int p0 = pre[a], p1 = pre[a + 1];
+  int last = 0;
+  if (lane == 0) {
+    part[t] = (double)gam;
+    part[cap + t] = (double)dlt;
+    part[2 * cap + t] = (double)rmax;
+    part[3 * cap + t] = (double)pmax;
+    part[4 * cap + t] = (double)bad;
+    __threadfence();
+    last = atomicAdd(&cnt[inst], 1u) == (unsigned)(p1 - p0 - 1);
+  }
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (!last) return;
+  __threadfence();
+  double G = 0.0, D = 0.0, R = 0.0, P = 0.0, Bd = 0.0;
+  for (int u = p0 + lane; u < p1; u += 32) {
+    G += __ldcg(part + u);
+    D += __ldcg(part + cap + u);
+    R = fmax(R, __ldcg(part + 2 * cap + u));
+    P = fmax(P, __ldcg(part + 3 * cap + u));
+    Bd = fmax(Bd, __ldcg(part + 4 * cap + u));
+  }
+  for (int o = 16; o > 0; o >>= 1) {   // fixed tree: deterministic
+    G += __shfl_down_sync(0xffffffffu, G, o);
+    D += __shfl_down_sync(0xffffffffu, D, o);
+    R = fmax(R, __shfl_down_sync(0xffffffffu, R, o));
+    P = fmax(P, __shfl_down_sync(0xffffffffu, P, o));
+    Bd = fmax(Bd, __shfl_down_sync(0xffffffffu, Bd, o));
+  }
+  if (lane == 0) {
+    cnt[inst] = 0u;
+    MixCtl *S = st + inst;
+    const bool init = S->first != 0;
+    S->first = 0;
+    cg_update(S, G, D, R, P, Bd, init);
+    if (S->done) {
+      alive[inst] = 0;
+      BatchDone *h = done + inst;
+      h->alpha = S->alpha;
+      h->beta = S->beta;
+      h->iter = S->iter;
+      h->status = S->status;
+      h->stalled = S->stalled;
+      h->F = S->F;
+      __threadfence_system();
+      h->done_seq = S->seq;
+      atomicExch(&bc->dirty, 1);
+    }
+  }
+}
+
+// The pass's last warp: keep the instances still iterating, in order, then
+// append the requests waiting in the ring (they start with the next pass,
+// launch set next_set).  The list is rewritten in place: a kept entry moves
+// to a position no later than its own, and every chunk is read before it is
+// written.
+__device__ void batch_list_update(const BInst *__restrict__ bi, MixCtl *st, int *act, int *pre,
+                                  unsigned *cnt, int *alive, BatchCtl *bc,
+                                  const BatchRing *ring, int ring_cap, int m, int TY,
+                                  int next_set) {
+  const int lane = threadIdx.x & 31;
+  int mnew = m, acc = __ldcg(&bc->ntiles);
+  long long nodes = (lane == 0) ? __ldcg(&bc->nodes) : 0;   // summed over the warp below
+  if (__ldcg(&bc->dirty)) {
+    mnew = 0;
+    acc = 0;
+    nodes = 0;
+    for (int base = 0; base < m; base += 32) {
+      const int a = base + lane;
+      const int inst = (a < m) ? act[a] : -1;
+      const bool keep = inst >= 0 && __ldcg(&alive[inst]) != 0;
+      const int T = keep ? bi[inst].tiles_x * ((bi[inst].ny + TY - 1) / TY) : 0;
+      if (keep) nodes += (long long)bi[inst].nx * bi[inst].ny;
+      const unsigned bal = __ballot_sync(0xffffffffu, keep);
+      int incl = T;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      if (keep) {
+        const int pos = mnew + __popc(bal & ((1u << lane) - 1u));
+        act[pos] = inst;
+        pre[pos] = acc + incl - T;
+      }
+      mnew += __popc(bal);
+      acc += __shfl_sync(0xffffffffu, incl, 31);
+    }
+  }
+  const int head = __ldcg(&bc->req_head);
+  const int tail = ld_acquire_sys(&ring->tail);   // every lane: orders its reads of ids
+  for (int base = head; base < tail; base += 32) {
+    const int k = base + lane;
+    const int inst = (k < tail) ? ring->ids[k % ring_cap] : -1;
+    const bool add = inst >= 0;
+    const int T = add ? bi[inst].tiles_x * ((bi[inst].ny + TY - 1) / TY) : 0;
+    if (add) nodes += (long long)bi[inst].nx * bi[inst].ny;
+    const unsigned bal = __ballot_sync(0xffffffffu, add);
+    int incl = T;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (add) {
+      const int pos = mnew + __popc(bal & ((1u << lane) - 1u));
+      act[pos] = inst;
+      pre[pos] = acc + incl - T;
+      st[inst].flip = next_set;
+      cnt[inst] = 0u;
+      alive[inst] = 1;
+    }
+    mnew += __popc(bal);
+    acc += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  for (int o = 16; o > 0; o >>= 1) nodes += __shfl_down_sync(0xffffffffu, nodes, o);
+  if (lane == 0) {
+    pre[mnew] = acc;
+    bc->m = mnew;
+    bc->ntiles = acc;
+    bc->req_head = tail;
+    bc->nodes = nodes;
+  }
+}
+
+template <int NS, int WPB>
+__global__ void __launch_bounds__(32 * WPB, WPB >= 7 ? 2 : 3)
+k_cg2d_batch(const __grid_constant__ CUtensorMap tm_r0, const __grid_constant__ CUtensorMap tm_r1,
+             const __grid_constant__ CUtensorMap tm_p0, const __grid_constant__ CUtensorMap tm_p1,
+             const __grid_constant__ CUtensorMap tm_s, const BInst *__restrict__ bi, MixCtl *st,
+             int *act, int *pre, unsigned *cnt, int *alive, BatchCtl *bc, int TY, int set,
+             float *r0, float *r1, float *p0, float *p1, float *__restrict__ d,
+             const float *__restrict__ xref, double *part, int part_cap, int P,
+             const BatchRing *ring, int ring_cap, BatchDone *done) {
+  constexpr int OR = 0, OP = kSlot, OS = 2 * kSlot;
+  constexpr int STAGE = 3 * kSlot;
+  constexpr int RING = 2 * kWin;
+  constexpr int WARP_FLOATS = NS * STAGE + 4 * RING;
+  static_assert((STAGE * 4) % 128 == 0 && (WARP_FLOATS * 4) % 128 == 0, "stage alignment");
+  extern __shared__ __align__(128) unsigned char cgb_raw[];
+  __shared__ __align__(8) uint64_t bars[WPB * NS];
+  __shared__ int ktabs[WPB * kTab];
+  const int m = bc->m;
+  const int ntot = bc->ntiles;
+  const long long nodes0 = bc->nodes;
+  float *cgb_smem = reinterpret_cast<float *>(
+      (reinterpret_cast<uintptr_t>(cgb_raw) + 127) & ~uintptr_t(127));
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int gw = blockIdx.x * WPB + wib, nw = gridDim.x * WPB;
+  const int steps = TY + 4;
+  const int my_tiles = (gw < ntot) ? (ntot - 1 - gw) / nw + 1 : 0;
+  const int nq = my_tiles * steps;
+  float *sb = cgb_smem + (size_t)wib * WARP_FLOATS;
+  float *ring_s = sb + NS * STAGE;
+  uint64_t *bar = bars + wib * NS;
+
+  // lane 0: the next row to copy (tile, step, atlas row of the tile's y0,
+  // the buffer set its instance reads)
+  int nx_q = 0, nx_j = 0, nx_x0 = 0, nx_row = 0, nx_dir = 1, nx_t = gw, nx_rs = 0;
+  auto set_tile = [&](int t) {
+    nx_t = t;
+    if (t >= ntot) return;
+    const int a = batch_find(pre, m, t);
+    const int inst = act[a];
+    const int local = t - pre[a];
+    const int tx = bi[inst].tiles_x;
+    const int cyk = local / tx;
+    nx_x0 = (local - cyk * tx) * kW;
+    nx_row = bi[inst].row0 + cyk * TY;
+    nx_dir = (cyk & 1) ? -1 : 1;
+    nx_rs = set ^ st[inst].flip;
+  };
+  auto issue_next = [&]() {
+    const int y = (nx_dir > 0) ? nx_row - 2 + nx_j : nx_row + TY + 1 - nx_j;
+    float *dst = sb + (nx_q % NS) * STAGE;
+    uint64_t *b = bar + (nx_q % NS);
+    mbar_expect_tx(b, 3u * kWin * 4u);
+    tma_load_2d(dst + OR, nx_rs ? &tm_r1 : &tm_r0, nx_x0 - 4, y, b);
+    tma_load_2d(dst + OP, nx_rs ? &tm_p1 : &tm_p0, nx_x0 - 4, y, b);
+    tma_load_2d(dst + OS, &tm_s, nx_x0 - 4, y, b);
+    ++nx_q;
+    if (++nx_j == steps) {
+      nx_j = 0;
+      set_tile(nx_t + nw);
+    }
+  };
+  if (lane == 0) {
+    for (int k = 0; k < NS; ++k) mbar_init(&bar[k], 1);
+    mbar_init_fence();
+    set_tile(gw);
+    while (nx_q < NS && nx_q < nq) issue_next();
+  }
+  __syncwarp();
+
+  bool fault = false;
+  int q = 0;
+  const int c = 4 + 4 * lane;
+  const bool l0 = lane == 0, l31 = lane == 31;
+  const int hA = l31 ? kW + 4 : 2;
+  const int hB = l31 ? kW + 4 : 3;
+  const int hI = l31 ? hB - 1 : hB + 1;
+  const int hO = l31 ? hB + 1 : hB - 1;
+  for (int k = 0; k < my_tiles && !fault; ++k) {
+    const int t = gw + k * nw;
+    const int a = batch_find(pre, m, t);
+    const int inst = act[a];
+    const int local = t - pre[a];
+    const BInst B = bi[inst];
+    const MixCtl *S = st + inst;
+    const float beta = (float)S->beta;
+    const float alpha = (float)S->alpha;
+    const int F = S->F, dF = S->dF, fd = S->fd;
+    const float gwr = p2f(-dF);
+    const float alphaF = (float)scalbn(S->alpha, F);
+    const bool check = S->mode != 0 && ((S->iter & 3) == 3);
+    const float thetaF = (float)scalbn((double)S->theta, -F);
+    const bool half = B.boundary == EIK_BOUNDARY_HALF_CELL;
+    float *r_out = (set ^ S->flip) ? r0 : r1;   // the other buffer set
+    float *p_out = (set ^ S->flip) ? p0 : p1;
+    Grid g{};
+    g.nx = B.nx;
+    g.ny = B.ny;
+    g.nz = 1;
+    g.boundary = B.boundary;
+    const CellGrid cg = B.cg;
+    const int *__restrict__ kx = B.kx;
+    const int64_t rowoff = (int64_t)B.row0 * P;
+    const int cyk = local / B.tiles_x;
+    const int x0 = (local - cyk * B.tiles_x) * kW;
+    const int y0 = cyk * TY;
+    const int dir = (cyk & 1) ? -1 : 1;
+    const int ystart = (dir > 0) ? y0 - 2 : y0 + TY + 1;
+    const int xl = x0 + 4 * lane;
+    float hx[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) hx[i] = (half && (xl + i == 0 || xl + i == g.nx - 1)) ? 0.5f : 1.f;
+    const int xh = l31 ? x0 + kW : x0 - 1;
+    const float hxh = (half && (xh == 0 || xh == g.nx - 1)) ? 0.5f : 1.f;
+    const int cmax = cg.cx - 1;
+    const int cxo = min(xl >> cg.lgB, cmax);
+    const int cxl = (xl >= 1) ? min((xl - 1) >> cg.lgB, cmax) : cxo;
+    const int cxr = (xl + 4 < g.nx) ? min((xl + 4) >> cg.lgB, cmax) : cxo;
+    const int cxh = l31 ? cxr : cxl;
+    const bool st_ok = xl < B.wx;
+    Fac2 fb{INT_MIN, 0}, fc{INT_MIN, 0};
+    KTab kt{nullptr, 0, 0, 1};
+    {
+      const int cr0 = max(y0 - 3, 0) >> cg.lgB, cr1 = min(y0 + TY + 2, g.ny - 1) >> cg.lgB;
+      const int cc0 = max(x0 - 1, 0) >> cg.lgB, cc1 = min(min(x0 + kW, g.nx - 1) >> cg.lgB, cmax);
+      const int nrow = cr1 - cr0 + 1, ncol = cc1 - cc0 + 1;
+      __syncwarp();
+      if (nrow * ncol <= kTab) {
+        int *tab = ktabs + wib * kTab;
+        for (int e = lane; e < nrow * ncol; e += 32)
+          tab[e] = __ldg(kx + (cr0 + e / ncol) * cg.cx + cc0 + e % ncol);
+        __syncwarp();
+        kt = KTab{tab, cr0, cc0, ncol};
+      }
+    }
+    float gam = 0.f, dlt = 0.f, rmax = 0.f, pmax = 0.f;
+    int bad = 0;
+    float4 dq0 = make_float4(0, 0, 0, 0), dq1 = dq0, dq2 = dq0;
+    float4 xq0 = dq0, xq1 = dq0, xq2 = dq0;
+
+    for (int j = 0; j < steps; ++j, ++q) {
+      float *S0 = sb + (q % NS) * STAGE;
+      bool ok = mbar_wait_bounded(&bar[q % NS], (uint32_t)(q / NS) & 1u);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) {
+        fault = true;
+        break;
+      }
+      const int y = ystart + dir * j;
+      if (j >= 2 && j < TY + 2 && y < g.ny && st_ok) {
+        const int64_t o = rowoff + (int64_t)y * P + xl;
+        dq0 = ld4(d + o);
+        if (check) xq0 = __ldg(reinterpret_cast<const float4 *>(xref + o));
+      }
+      // ---- A: row y_j, p in place
+      {
+        const float4 r4 = ld4(S0 + OR + c), p4 = ld4(S0 + OP + c);
+        st4(S0 + OP + c, fmaf(beta, p4.x, r4.x), fmaf(beta, p4.y, r4.y),
+            fmaf(beta, p4.z, r4.z), fmaf(beta, p4.w, r4.w));
+        if (l0 || l31) {
+          const float2 r2 = *reinterpret_cast<const float2 *>(S0 + OR + hA);
+          const float2 p2 = *reinterpret_cast<const float2 *>(S0 + OP + hA);
+          *reinterpret_cast<float2 *>(S0 + OP + hA) =
+              make_float2(fmaf(beta, p2.x, r2.x), fmaf(beta, p2.y, r2.y));
+        }
+      }
+      __syncwarp();
+      // ---- B: row y_{j-1}
+      if (j >= 2) {
+        const int y1 = y - dir;
+        const float *S1 = sb + ((q - 1) % NS) * STAGE;
+        const float *S2 = sb + ((q - 2) % NS) * STAGE;
+        float *RB = ring_s + ((q - 1) & 3) * RING;
+        const float hy1 = (half && (y1 == 0 || y1 == g.ny - 1)) ? 0.5f : 1.f;
+        const float4 r4 = ld4(S1 + OR + c), s4 = ld4(S1 + OS + c);
+        float rn[4];
+        const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
+        {
+          fac2_update(fb, y1, dir, g, cg, kx, kt, cxo, cxl, cxr, cxh, fd);
+          const float4 p4 = ld4(S1 + OP + c);
+          const float4 uc = mul4(s4, p4);
+          const float4 up = mul4(ld4(S2 + OS + c), ld4(S2 + OP + c));
+          const float4 un = mul4(ld4(S0 + OS + c), ld4(S0 + OP + c));
+          const float uL = S1[OS + c - 1] * S1[OP + c - 1], uR = S1[OS + c + 4] * S1[OP + c + 4];
+          const float xs[4] = {fmaf(uL, fb.fL, uc.y), uc.x + uc.z, uc.y + uc.w,
+                               fmaf(uR, fb.fR, uc.z)};
+          const float ysP[4] = {up.x, up.y, up.z, up.w}, ysN[4] = {un.x, un.y, un.z, un.w};
+          const float pv[4] = {p4.x, p4.y, p4.z, p4.w}, rv[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float ys = fmaf(ysP[i], fb.fP, ysN[i] * fb.fN);
+            const float acc = fmaf(hy1, xs[i], hx[i] * ys);
+            rn[i] = fmaf(-alpha, fmaf(-sv[i], acc, pv[i]), rv[i]);
+          }
+        }
+        st4(RB + c, rn[0], rn[1], rn[2], rn[3]);
+        st4(RB + kWin + c, sv[0] * rn[0], sv[1] * rn[1], sv[2] * rn[2], sv[3] * rn[3]);
+        if (l0 || l31) {
+          const float sh = S1[OS + hB];
+          float rh = S1[OR + hB];
+          const float uin = S1[OS + hI] * S1[OP + hI];
+          const float uout = S1[OS + hO] * S1[OP + hO];
+          const float upv = S2[OS + hB] * S2[OP + hB], unv = S0[OS + hB] * S0[OP + hB];
+          const float acc = fmaf(hy1, fmaf(uin, fb.fxh, uout),
+                                 hxh * fmaf(upv, fb.fPh, unv * fb.fNh));
+          rh = fmaf(-alpha, fmaf(-sh, acc, S1[OP + hB]), rh);
+          RB[hB] = rh;
+          RB[kWin + hB] = sh * rh;
+        }
+      }
+      __syncwarp();
+      // ---- C: row y_{j-2}
+      if (j >= 4) {
+        const int y2 = y - 2 * dir;
+        if (y2 < g.ny) {
+          fac2_update(fc, y2, dir, g, cg, kx, kt, cxo, cxl, cxr, cxh, fd);
+          const float *S2 = sb + ((q - 2) % NS) * STAGE;
+          const float *Rc = ring_s + ((q - 2) & 3) * RING;
+          const float *Rp = ring_s + ((q - 3) & 3) * RING;
+          const float *Rn = ring_s + ((q - 1) & 3) * RING;
+          const float hy2 = (half && (y2 == 0 || y2 == g.ny - 1)) ? 0.5f : 1.f;
+          const float4 nc = ld4(Rc + kWin + c), np = ld4(Rp + kWin + c), nn = ld4(Rn + kWin + c);
+          const float4 rn4 = ld4(Rc + c), s4 = ld4(S2 + OS + c);
+          const float nL = Rc[kWin + c - 1], nR = Rc[kWin + c + 4];
+          const float xs[4] = {fmaf(nL, fc.fL, nc.y), nc.x + nc.z, nc.y + nc.w,
+                               fmaf(nR, fc.fR, nc.z)};
+          const float ysP[4] = {np.x, np.y, np.z, np.w}, ysN[4] = {nn.x, nn.y, nn.z, nn.w};
+          const float rv[4] = {rn4.x, rn4.y, rn4.z, rn4.w}, sv[4] = {s4.x, s4.y, s4.z, s4.w};
+          const float4 p4 = ld4(S2 + OP + c);
+          const float pv[4] = {p4.x, p4.y, p4.z, p4.w};
+          const float dv[4] = {dq2.x, dq2.y, dq2.z, dq2.w};
+          const float xv[4] = {xq2.x, xq2.y, xq2.z, xq2.w};
+          float dn[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float ys = fmaf(ysP[i], fc.fP, ysN[i] * fc.fN);
+            const float acc = fmaf(hy2, xs[i], hx[i] * ys);
+            const float wv = fmaf(-sv[i], acc, rv[i]);
+            const float tt = rv[i] * fc.W;
+            gam = fmaf(tt, rv[i], gam);
+            dlt = fmaf(tt, wv, dlt);
+            rmax = fmaxf(rmax, fabsf(rv[i]));
+            dn[i] = fmaf(alphaF, pv[i], dv[i]);
+            pmax = fmaxf(pmax, fabsf(pv[i]));
+            if (check && fabsf(rv[i]) > thetaF * fabsf(xv[i] + dn[i])) bad = 1;
+          }
+          if (st_ok) {
+            const int64_t o = rowoff + (int64_t)y2 * P + xl;
+            st4(d + o, dn[0], dn[1], dn[2], dn[3]);
+            st4(r_out + o, rv[0] * gwr, rv[1] * gwr, rv[2] * gwr, rv[3] * gwr);
+            st4(p_out + o, pv[0] * gwr, pv[1] * gwr, pv[2] * gwr, pv[3] * gwr);
+          }
+        }
+      }
+      dq2 = dq1;
+      dq1 = dq0;
+      xq2 = xq1;
+      xq1 = xq0;
+      __syncwarp();
+      if (l0 && q >= 2 && nx_q < nq) {
+        fence_proxy_async();
+        issue_next();
+      }
+    }
+    if (fault) break;
+    batch_tile_done(gam, dlt, rmax, pmax, bad, t, inst, a, pre, st, cnt, alive, bc, part,
+                    part_cap, done);
+  }
+  if (fault && l0) {
+    for (int qq = q; qq < nx_q; ++qq) mbar_wait_bounded(&bar[qq % NS], (uint32_t)(qq / NS) & 1u);
+    atomicExch(&bc->fault, 1);
+  }
+  __syncwarp();
+  // end of the pass for this warp; the last one updates the list
+  int lastw = 0;
+  if (l0) {
+    __threadfence();
+    lastw = atomicAdd(&bc->warps_done, 1u) == (unsigned)(nw - 1);
+  }
+  lastw = __shfl_sync(0xffffffffu, lastw, 0);
+  if (!lastw) return;
+  __threadfence();
+  batch_list_update(bi, st, act, pre, cnt, alive, bc, ring, ring_cap, m, TY, set ^ 1);
+  if (l0) {
+    bc->warps_done = 0u;
+    bc->dirty = 0;
+    if (m > 0) {
+      bc->passes += 1;
+      bc->work += nodes0;
+    }
+  }
 }
 
 // ------------------------------------------------------------------ 3D pass
@@ -1065,6 +1543,33 @@ bool plan3d(Cg32Plan *pl, const Grid &g, int num_sms) {
   }
 }
 
+// packed batch: the 2D variants of the single-grid pass
+template <int NS, int WPB>
+bool plan2db_t(Cg32BatchPlan *pl, int num_sms) {
+  const size_t sm = smem2d<NS, WPB>();
+  if (cudaFuncSetAttribute(k_cg2d_batch<NS, WPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sm) != cudaSuccess)
+    return false;
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cg2d_batch<NS, WPB>, 32 * WPB, sm) !=
+          cudaSuccess ||
+      per < 1)
+    return false;
+  pl->ns = NS;
+  pl->wpb = WPB;
+  pl->smem = sm;
+  pl->nblk = per * num_sms;
+  return true;
+}
+
+template <int NS, int WPB>
+void launch2db_t(const Cg32BatchPlan &pl, const Cg32BatchBuffers &b, int set, cudaStream_t s) {
+  k_cg2d_batch<NS, WPB><<<pl.nblk, 32 * WPB, pl.smem, s>>>(
+      pl.tm_r[0], pl.tm_r[1], pl.tm_p[0], pl.tm_p[1], pl.tm_s, b.bi, b.st, b.act, b.pre, b.cnt,
+      b.alive, b.bc, pl.ty, set, b.r[0], b.r[1], b.p[0], b.p[1], b.d, b.xref, b.part, b.part_cap,
+      b.P, b.ring, b.ring_cap, b.done);
+}
+
 }  // namespace
 
 int cg32_max_blocks(int ndim, int num_sms) { return 8 * num_sms; }
@@ -1115,6 +1620,50 @@ void cg32_iter(const Cg32Plan &pl, const Grid &g, const CellGrid &cg, const Cg32
     launch2d<false>(pl, g, cg, b, set, s);
   else
     launch3d<false>(pl, g, cg, b, set, s);
+}
+
+bool cg32_batch_plan(Cg32BatchPlan *pl, const Cg32BatchBuffers &b, int num_sms, int variant,
+                     int ty, const char **why) {
+  if (!encode_fn()) {
+    *why = "cuTensorMapEncodeTiled is not available";
+    return false;
+  }
+  if (ty < 1 || variant < 0 || variant > 4) {
+    *why = "invalid batch tile shape";
+    return false;
+  }
+  pl->variant = variant == 0 ? 1 : variant;
+  pl->ty = ty;
+  bool planned = false;
+  switch (pl->variant) {
+    case 2: planned = plan2db_t<6, 4>(pl, num_sms); break;
+    case 3: planned = plan2db_t<7, 4>(pl, num_sms); break;
+    case 4: planned = plan2db_t<6, 7>(pl, num_sms); break;
+    default: planned = plan2db_t<5, 5>(pl, num_sms); break;
+  }
+  if (!planned) {
+    *why = "cannot configure the packed inner-CG kernels on this device";
+    cudaGetLastError();
+    return false;
+  }
+  bool ok = true;
+  for (int k = 0; k < 2; ++k) {
+    ok = ok && encode_f32(&pl->tm_r[k], b.r[k], b.P, b.P, b.H, 0, kWin, 1, 1);
+    ok = ok && encode_f32(&pl->tm_p[k], b.p[k], b.P, b.P, b.H, 0, kWin, 1, 1);
+  }
+  ok = ok && encode_f32(&pl->tm_s, b.s32, b.P, b.P, b.H, 0, kWin, 1, 1);
+  if (!ok) *why = "cannot encode the atlas tensor maps";
+  return ok;
+}
+
+void cg32_batch_pass(const Cg32BatchPlan &pl, const Cg32BatchBuffers &b, int set,
+                     cudaStream_t s) {
+  switch (pl.variant) {
+    case 2: launch2db_t<6, 4>(pl, b, set, s); break;
+    case 3: launch2db_t<7, 4>(pl, b, set, s); break;
+    case 4: launch2db_t<6, 7>(pl, b, set, s); break;
+    default: launch2db_t<5, 5>(pl, b, set, s); break;
+  }
 }
 
 }  // namespace eik

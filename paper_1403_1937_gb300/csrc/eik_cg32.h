@@ -70,6 +70,10 @@ struct MixCtl {
   int stalled;       // the recurrence lost positivity: the solve ended early
   int fault;         // a bounded device-side wait expired
   int withhold;      // test hook: one warp never gets its first copy
+  // packed batches (the single-grid passes ignore these)
+  int first;         // the next pass is the inner solve's first (w = A r only)
+  int flip;          // the instance reads buffer set (launch set ^ flip)
+  int seq;           // request number, echoed in the host record when done
   unsigned int counter[4];
 };
 
@@ -110,5 +114,88 @@ void cg32_init(const Cg32Plan &pl, const Grid &g, const CellGrid &cg, const Cg32
 // One inner iteration: reads buffer set `set`, writes set 1 - set.
 void cg32_iter(const Cg32Plan &pl, const Grid &g, const CellGrid &cg, const Cg32Buffers &b,
                int set, cudaStream_t s);
+
+// ------------------------------------------------- packed 2D batches
+// Many 2D instances share one set of FP32 arrays (the "atlas"): instance i
+// occupies rows row0 .. row0 + ny - 1 of a pitched array of P columns (P >= every
+// nx, a multiple of 4), with at least two zero rows between instances and zero
+// columns right of each instance.  So a tile's two-row halo and its columns
+// past nx read zeros, as they would from a single grid's out-of-bounds fill,
+// and one set of tensor maps serves every instance.
+struct BInst {
+  int nx, ny;
+  int wx;            // columns written per row: nx rounded up to 4
+  int row0;          // atlas row of y = 0
+  int tiles_x;       // 128-column tiles
+  int boundary;      // EIK_BOUNDARY_*
+  CellGrid cg;
+  const int *kx;     // the instance's cell exponents
+};
+
+// Pass-level state of a packed batch.  act[0 .. m) lists the instances still
+// iterating and pre[0 .. m] the prefix sums of their tile counts: list
+// position t belongs to act[a] with pre[a] <= t < pre[a + 1].
+struct BatchCtl {
+  int m;               // active instances
+  int ntiles;          // pre[m]
+  int dirty;           // an instance finished during this pass
+  int fault;           // a bounded device-side wait expired
+  unsigned warps_done; // ticket of the pass's last warp
+  int passes;          // passes that had work, since the list was set
+  int req_head;        // requests admitted so far (see BatchRing)
+  int pad;
+  long long nodes;     // nodes of the instances in the list
+  long long work;      // sum over passes of the nodes they covered
+};
+
+// Requests to join the tile list, in mapped host memory: the host writes
+// ids[tail % cap] and then advances tail; the last warp of every pass admits
+// ids[head .. tail) for the next pass.
+struct BatchRing {
+  volatile int tail;
+  int pad[31];
+  volatile int ids[1];   // cap entries (allocated with the ring)
+};
+
+// What the host learns when an instance's inner solve ends, in mapped host
+// memory: the finisher writes the fields, then done_seq = the request number.
+struct BatchDone {
+  double alpha, beta;
+  int iter, status, stalled, F;
+  volatile int done_seq;
+  int pad[7];
+};
+
+struct Cg32BatchBuffers {
+  float *r[2], *p[2], *s32, *d, *xref;   // atlas arrays, pitch P
+  int P, H;                              // pitch and rows of the atlas
+  const BInst *bi;
+  MixCtl *st;            // one control block per instance
+  int *act, *pre;        // active list (device)
+  unsigned *cnt;         // per-instance tile tickets of the current pass
+  int *alive;            // 1 while an instance is in the list and iterating
+  BatchCtl *bc;
+  double *part;          // 5 x part_cap per-tile partials
+  int part_cap;
+  BatchRing *ring;       // device view of the mapped request ring
+  int ring_cap;
+  BatchDone *done;       // device view of the mapped completion records
+};
+
+struct Cg32BatchPlan {
+  int variant = 0, ty = 0, nblk = 0, wpb = 0, ns = 0;
+  size_t smem = 0;
+  CUtensorMap tm_r[2], tm_p[2], tm_s;
+};
+
+// Launch geometry of the packed passes (variant as cg32_plan's 2D table, ty
+// rows per tile) and the atlas tensor maps.
+bool cg32_batch_plan(Cg32BatchPlan *pl, const Cg32BatchBuffers &b, int num_sms, int variant,
+                     int ty, const char **why);
+// One pass over every tile of the active instances (launch buffer set `set`;
+// an instance whose MixCtl.first is set makes it its inner solve's first
+// pass), then the admission of waiting requests for the next pass.
+void cg32_batch_pass(const Cg32BatchPlan &pl, const Cg32BatchBuffers &b, int set,
+                     cudaStream_t s);
 
 }  // namespace eik

@@ -34,6 +34,7 @@
 #include <string>
 #include <vector>
 
+#include "eik_batch.h"
 #include "eik_cg32.h"
 #include "eik_launch.h"
 #include "eik_mixed.h"
@@ -458,6 +459,10 @@ struct MixedState {
   int *kx = nullptr;
   double *x64 = nullptr, *part = nullptr;
   MixCtl *st = nullptr, *h_st = nullptr;
+  // member of a packed batch: the FP32 arrays and st belong to the batch,
+  // and inner solves run through it
+  BatchExec *batch = nullptr;
+  int bidx = -1;
   cudaGraphExec_t graph = nullptr;
   int64_t launches[8] = {0};
   // per-launch CUDA-event timing of the inner passes when profiling
@@ -514,9 +519,8 @@ static bool mal(T **p, size_t n) {
   return cudaMalloc((void **)p, sizeof(T) * (n ? n : 1)) == cudaSuccess;
 }
 
-eik_status mixed_create(MixedState **out, const Grid &g, const TileCount &tc, int num_sms,
-                        int tile_override, cudaStream_t s) {
-  MixedState *m = new MixedState();
+// Cell grid, launch sizes and the FP64 / cell arrays of a solver.
+static void mixed_layout(MixedState *m, const Grid &g, const TileCount &tc, int num_sms) {
   m->g = g;
   m->tc = tc;
   // cell edge: power of two >= 16 with at most kMaxCells cells
@@ -543,6 +547,20 @@ eik_status mixed_create(MixedState **out, const Grid &g, const TileCount &tc, in
   m->nblk_stencil = (int)std::min<int64_t>(tc.total, (int64_t)per_sm * num_sms);
   m->cap = num_sms * 8;
   m->nblk_part = std::max(std::max(m->nblk_stencil, m->cap), cg32_max_blocks(g.ndim, num_sms));
+}
+
+// The attribute belongs to the function, not to one solver: set it to the
+// largest cell grid any solver can use, so concurrent solvers agree.
+static bool coarse_smem_attr() {
+  const size_t smem = 2 * sizeof(float) * kMaxCells;
+  return cudaFuncSetAttribute(k_coarse_exponents, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem) == cudaSuccess;
+}
+
+eik_status mixed_create(MixedState **out, const Grid &g, const TileCount &tc, int num_sms,
+                        int tile_override, cudaStream_t s) {
+  MixedState *m = new MixedState();
+  mixed_layout(m, g, tc, num_sms);
   // row pitch of the FP32 arrays: a multiple of 4 elements (16-byte rows for
   // the tensor maps and the float4 accesses of the inner passes)
   m->px = (g.nx + 3) / 4 * 4;
@@ -585,11 +603,7 @@ eik_status mixed_create(MixedState **out, const Grid &g, const TileCount &tc, in
     g_msg = std::string("inner CG: ") + why;
     return EIK_ERR_CUDA;
   }
-  // the attribute belongs to the function, not to this solver: set it to the
-  // largest cell grid any solver can use, so concurrent solvers agree
-  const size_t smem = 2 * sizeof(float) * kMaxCells;
-  if (cudaFuncSetAttribute(k_coarse_exponents, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem) != cudaSuccess) {
+  if (!coarse_smem_attr()) {
     cudaGetLastError();
     mixed_destroy(m);
     g_msg = "cannot reserve shared memory for the coarse estimate";
@@ -599,15 +613,59 @@ eik_status mixed_create(MixedState **out, const Grid &g, const TileCount &tc, in
   return EIK_OK;
 }
 
+eik_status mixed_create_member(MixedState **out, const Grid &g, const TileCount &tc,
+                               int num_sms, BatchExec *batch, int idx, cudaStream_t s) {
+  if (g.ndim != 2) {
+    g_msg = "packed batches are two-dimensional";
+    return EIK_ERR_ARG;
+  }
+  MixedState *m = new MixedState();
+  mixed_layout(m, g, tc, num_sms);
+  const BatchMember bm = batch_exec_member(batch, idx);
+  m->batch = batch;
+  m->bidx = idx;
+  m->px = bm.P;
+  m->s32 = bm.s32;
+  m->d32 = bm.d;
+  m->xref = bm.xref;
+  m->r32[0] = bm.r0;
+  m->p32[0] = bm.p0;
+  m->st = bm.st;
+  bool ok = mal(&m->x64, g.n) && mal(&m->fb, m->cg.ncell) && mal(&m->St, m->cg.ncell) &&
+            mal(&m->kx, m->cg.ncell) && mal(&m->part, 8 * (size_t)m->nblk_part);
+  if (ok) ok = cudaMallocHost((void **)&m->h_st, sizeof(MixCtl)) == cudaSuccess;
+  if (ok) ok = cudaMemsetAsync(m->kx, 0, sizeof(int) * m->cg.ncell, s) == cudaSuccess &&
+               cudaStreamSynchronize(s) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    mixed_destroy(m);
+    g_msg = "device allocation failed";
+    return EIK_ERR_OOM;
+  }
+  if (!coarse_smem_attr()) {
+    cudaGetLastError();
+    mixed_destroy(m);
+    g_msg = "cannot reserve shared memory for the coarse estimate";
+    return EIK_ERR_CUDA;
+  }
+  batch_exec_set_cells(batch, idx, m->cg, m->kx);
+  *out = m;
+  return EIK_OK;
+}
+
 void mixed_destroy(MixedState *m) {
   if (!m) return;
   if (m->graph) cudaGraphExecDestroy(m->graph);
   for (auto &e : m->ev)
     if (e) cudaEventDestroy(e);
-  void *ptrs[] = {m->s32, m->xref, m->fb, m->St, m->d32, m->r32[0], m->r32[1], m->p32[0],
-                  m->p32[1], m->kx, m->x64, m->part, m->st};
-  for (void *p : ptrs)
+  void *own[] = {m->fb, m->St, m->kx, m->x64, m->part};
+  for (void *p : own)
     if (p) cudaFree(p);
+  if (!m->batch) {   // a member's FP32 arrays and control block are the batch's
+    void *fp32[] = {m->s32, m->xref, m->d32, m->r32[0], m->r32[1], m->p32[0], m->p32[1], m->st};
+    for (void *p : fp32)
+      if (p) cudaFree(p);
+  }
   if (m->h_st) cudaFreeHost(m->h_st);
   delete m;
 }
@@ -712,42 +770,59 @@ static eik_status refine(MixedState *m, const MixedArgs &a, int lo, int hi, int 
     st.mode = (outer == 0 || !std::isfinite(cw)) ? 0 : 1;
     st.thresh = (float)(red * st.r_inf);
     st.theta = (float)std::max(0.5 * tol, 1e-3 * cw);
+    if (m->batch) {
+      // the batch's passes make the first pass of this solve w = A r
+      st.seq = batch_exec_ticket(m->batch, m->bidx);
+      st.first = 1;
+    }
     *m->h_st = st;
     MCK(cudaMemcpyAsync(m->st, m->h_st, sizeof(MixCtl), cudaMemcpyHostToDevice, s));
-    if (m->profile && !m->ev[0])
-      for (auto &e : m->ev) MCK(cudaEventCreate(&e));
-    if (m->profile) MCK(cudaEventRecord(m->ev[0], s));
-    cg32_init(m->plan, g, m->cg, m->bufs, 0, s);
-    m->launches[3]++;
-    MCK(cudaGetLastError());
-    if (m->profile) {
-      MCK(cudaEventRecord(m->ev[1], s));
+    if (m->batch) {
+      // joins the batch's tile list at its next pass; returns when it ends
       MCK(cudaStreamSynchronize(s));
-      float t = 0.f;
-      MCK(cudaEventElapsedTime(&t, m->ev[0], m->ev[1]));
-      m->ms[3] += t;
-      m->timed[3] += 1;
-    }
-    for (int it = 0;; ++it) {
+      const eik_status bs = batch_exec_inner(m->batch, m->bidx, st.seq, m->h_st);
+      if (bs != EIK_OK) {
+        g_msg = batch_exec_error(m->batch);
+        result = bs;
+        break;
+      }
+      m->launches[4] += m->h_st->iter + 1;
+    } else {
+      if (m->profile && !m->ev[0])
+        for (auto &e : m->ev) MCK(cudaEventCreate(&e));
+      if (m->profile) MCK(cudaEventRecord(m->ev[0], s));
+      cg32_init(m->plan, g, m->cg, m->bufs, 0, s);
+      m->launches[3]++;
+      MCK(cudaGetLastError());
       if (m->profile) {
-        // one timed iteration per host check: no launch runs past convergence
         MCK(cudaEventRecord(m->ev[1], s));
-        cg32_iter(m->plan, g, m->cg, m->bufs, it & 1, s);
-        MCK(cudaEventRecord(m->ev[2], s));
-        m->launches[4] += 1;
-      } else {
-        MCK(cudaGraphLaunch(m->graph, s));
-        m->launches[4] += kInnerGraphIters;
-      }
-      MCK(cudaMemcpyAsync(m->h_st, m->st, sizeof(MixCtl), cudaMemcpyDeviceToHost, s));
-      MCK(cudaStreamSynchronize(s));
-      if (m->profile) {
+        MCK(cudaStreamSynchronize(s));
         float t = 0.f;
-        MCK(cudaEventElapsedTime(&t, m->ev[1], m->ev[2]));
-        m->ms[4] += t;
-        m->timed[4] += 1;
+        MCK(cudaEventElapsedTime(&t, m->ev[0], m->ev[1]));
+        m->ms[3] += t;
+        m->timed[3] += 1;
       }
-      if (m->h_st->done) break;
+      for (int it = 0;; ++it) {
+        if (m->profile) {
+          // one timed iteration per host check: no launch runs past convergence
+          MCK(cudaEventRecord(m->ev[1], s));
+          cg32_iter(m->plan, g, m->cg, m->bufs, it & 1, s);
+          MCK(cudaEventRecord(m->ev[2], s));
+          m->launches[4] += 1;
+        } else {
+          MCK(cudaGraphLaunch(m->graph, s));
+          m->launches[4] += kInnerGraphIters;
+        }
+        MCK(cudaMemcpyAsync(m->h_st, m->st, sizeof(MixCtl), cudaMemcpyDeviceToHost, s));
+        MCK(cudaStreamSynchronize(s));
+        if (m->profile) {
+          float t = 0.f;
+          MCK(cudaEventElapsedTime(&t, m->ev[1], m->ev[2]));
+          m->ms[4] += t;
+          m->timed[4] += 1;
+        }
+        if (m->h_st->done) break;
+      }
     }
     total += m->h_st->iter;
     ++outer;
@@ -796,8 +871,10 @@ eik_status mixed_solve(MixedState *m, const MixedArgs &a, int *inner_iters, int 
   m->launches[0] += 3;
   m->launches[1] += 1;
   MCK(cudaGetLastError());
-  eik_status gs = build_graph(m, s);
-  if (gs != EIK_OK) return gs;
+  if (!m->batch) {
+    eik_status gs = build_graph(m, s);
+    if (gs != EIK_OK) return gs;
+  }
 
   const int band_bits = (a.opt.band_bits > 0) ? a.opt.band_bits : kBandBits;
   int kmin = 0, kmax = 0;

@@ -7,6 +7,7 @@
 namespace eik {
 
 struct MixedState;
+struct BatchExec;
 
 struct MixedArgs {
   Grid g;
@@ -30,6 +31,11 @@ struct MixedArgs {
 
 eik_status mixed_create(MixedState **out, const Grid &g, const TileCount &tc, int num_sms,
                         int tile_override, cudaStream_t s);
+// A member of a packed 2D batch: its FP32 inner-CG arrays and control block
+// are instance idx's in the batch's atlas, and its inner solves run through
+// the batch (eik_batch.h).
+eik_status mixed_create_member(MixedState **out, const Grid &g, const TileCount &tc,
+                               int num_sms, BatchExec *batch, int idx, cudaStream_t s);
 eik_status mixed_solve(MixedState *m, const MixedArgs &a, int *inner_iters, int *outer_iters,
                        double *res_cw, double *res_nw);
 // Writes S (and phi if non-null) from the refined iterate; device pointers.

@@ -61,7 +61,8 @@ def make_options(precision: str = "fp64", tol: Optional[float] = None,
                  stop_norm: str = "componentwise", max_iter: Optional[int] = None,
                  boundary: str = "half_cell", inner_tol: float = 0.0,
                  max_outer: int = 0, tile_override: int = 0,
-                 band_bits: int = 0, test_flags: int = 0) -> _lib.Options:
+                 band_bits: int = 0, test_flags: int = 0, batch_pack: int = 0,
+                 batch_tile_rows: int = 0) -> _lib.Options:
     o = _lib.default_options()
     o.precision = {"fp64": _lib.PREC_FP64, "mixed": _lib.PREC_MIXED}[precision]
     if tol is not None:
@@ -77,6 +78,8 @@ def make_options(precision: str = "fp64", tol: Optional[float] = None,
     o.tile_override = int(tile_override)
     o.band_bits = int(band_bits)
     o.test_flags = int(test_flags)
+    o.batch_pack = int(batch_pack)
+    o.batch_tile_rows = int(batch_tile_rows)
     return o
 
 
@@ -306,6 +309,23 @@ def eik_grad_batch(batch: Batch, dLdS, dLdf_out=None):
     stats = (_lib.Stats * len(batch.dims))()
     _lib.check(_lib.load().eik_grad_batch(batch.ptr, ip, op, ctypes.cast(stats, ctypes.c_void_p)))
     return dLdf_out, [s.as_dict() for s in stats]
+
+
+def eik_batch_info(batch: Batch) -> dict:
+    """How the batch runs (C: ``eik_batch_info``): packed or not, the packed
+    pass's variant and rows per tile, how they were chosen ("fixed",
+    "measured", "cached"), the packed pass launches so far, and over the
+    solves the node-passes covered and the device time of their graphs."""
+    pk, v, ty, how = (ctypes.c_int() for _ in range(4))
+    passes, work = ctypes.c_int64(), ctypes.c_int64()
+    ms = ctypes.c_double()
+    _lib.check(_lib.load().eik_batch_info(batch.ptr, ctypes.byref(pk), ctypes.byref(v),
+                                          ctypes.byref(ty), ctypes.byref(how),
+                                          ctypes.byref(passes), ctypes.byref(work),
+                                          ctypes.byref(ms)))
+    return {"packed": bool(pk.value), "variant": v.value, "tile_rows": ty.value,
+            "tuned": ("fixed", "measured", "cached")[how.value], "passes": passes.value,
+            "node_passes": work.value, "pass_ms": ms.value}
 
 
 def eik_destroy_batch(batch: Batch) -> None:

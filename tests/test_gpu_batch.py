@@ -38,9 +38,11 @@ def test_batch_small_c4(eik, precision):
 
 
 def test_batch_equals_single_solves(eik):
+    """Per-instance batches (each instance on its own stream) run exactly the
+    single-solve kernels: bit-identical results."""
     import torch
     insts = wl.config4(count=5, side=(64, 160))
-    opt = eik.make_options(precision="mixed", tol=1e-7)
+    opt = eik.make_options(precision="mixed", tol=1e-7, batch_pack=-1)
     b = eik.eik_create_batch(insts, opt, workers=3)
     S, _ = eik.eik_solve_batch(b)
     parts = b.split(S.cpu().numpy())
