@@ -180,6 +180,20 @@ def kernel_source_hash(files):
     return h.hexdigest()[:16]
 
 
+def ncu_traffic_field(kernel, workload_name, field):
+    """One field of a committed ncu summary entry, or None when absent or
+    taken on a different kernel source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    e = d.get(f"{kernel}@{workload_name}")
+    if not e or e.get("source_sha") != kernel_source_hash(e.get("source_files", [])):
+        return None
+    return e.get(field)
+
+
 def ncu_traffic(kernel, workload_name):
     """DRAM bytes per launch of ``kernel`` from the committed ncu summary, or
     None when absent or taken on a different kernel source."""
@@ -545,9 +559,13 @@ def run_batch(args):
         sec = (info1["pass_ms"] - info0["pass_ms"]) * 1e-3
         npass = info1["passes"] - info0["passes"]
         achieved = ALGO_BYTES_PER_NODE["mixed_cg"] * work / sec / 1e9
+        # DRAM bytes per node from the committed ncu capture of an all-active
+        # pass, times the nodes an average pass covered
+        per_node = ncu_traffic_field("mixed_cg_packed", "c4", "dram_bytes_per_node")
+        traffic = round(per_node * work / max(npass, 1)) if per_node else None
         roof = {"bound": "hbm", "kernel": "mixed_cg_packed (k_cg2d_batch)",
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
+                "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": peak_src,
                 "algorithmic_bytes_per_launch": round(ALGO_BYTES_PER_NODE["mixed_cg"] * work
                                                       / max(npass, 1)),

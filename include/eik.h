@@ -338,6 +338,39 @@ eik_status eik_backtrack(int ndim, const int64_t *dims, double h, const double *
 eik_status eik_sfs_forcing(const double *P, int64_t n, double f_min, double *f,
                            eik_stream_t stream);
 
+/*
+ * FFT perturbation series (Sec. 5, Table 1) on a 2D grid: with a constant
+ * f~, phi = phi_0 - phi_1 + ... + (-1)^T phi_T where phi_0 = G~ * delta_kron
+ * (G~(x) = exp(-f~|x|/hbar), sources as Kronecker deltas: Sec. 3.2,
+ * Eq. forcedPhiEquation) and phi_i = h^2 G * [(f^2 - f~^2) phi_{i-1}]
+ * (Eqs. phiRecRelation, phi_i_Solution; G = K_0(f~|x|/hbar)/(2 pi hbar^2),
+ * Eq. GreensFunction2D, averaged over the grid cell at the origin); then
+ * S = -hbar log phi (Eq. SfromPhi).  Convolutions are linear over the grid,
+ * by FP64 transforms of arrays zero-padded to the next power of two
+ * >= 2n - 1 per axis.  This is the paper's first solver, kept as a second
+ * workload: the finite-difference solve above is the main path.
+ *   dims        (nx, ny), each 2 .. 4096; node (x, y) is f[x + nx y].
+ *   h, hbar     > 0.
+ *   f           nx ny values, > 0 (host or device).
+ *   src_idx     nsrc >= 1 flat node indices (host or device).
+ *   terms       T, 0 .. 64.
+ *   f_tilde     f~; 0 = sqrt((f_min^2 + f_max^2)/2) (Eq. fTildeValue), which
+ *               makes the series converge (Sec. 5.1).
+ *   S_out       nx ny values (host or device, caller-owned); NaN where the
+ *               truncated series or the transforms' rounding (absolute errors
+ *               near 1e-16 max phi, the paper's reason for MPFR) leave
+ *               phi <= 0.
+ *   phi_out     nx ny values or NULL.
+ *   f_tilde_out the f~ used, or NULL.
+ * Allocates its work arrays (about 48 bytes per padded node), runs on
+ * `stream` and returns when the outputs are written.  EIK_ERR_ARG for bad
+ * sizes, pointers, values or f not finite and positive; EIK_ERR_OOM.
+ */
+eik_status eik_fft_series(const int64_t *dims, double h, double hbar, const double *f,
+                          const int64_t *src_idx, int64_t nsrc, int terms, double f_tilde,
+                          double *S_out, double *phi_out, double *f_tilde_out,
+                          eik_stream_t stream);
+
 /* Per-kernel counters of a handle (diagnostics; the paper has no
  * counterpart).  launches counts every kernel launch the handle issued since
  * creation or the last eik_reset_kernel_stats (kernels inside captured graphs

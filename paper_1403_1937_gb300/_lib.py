@@ -103,6 +103,9 @@ _SIGS = [
      [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_double, _P, _P, ctypes.c_int64,
       ctypes.c_double, ctypes.c_int, _P, ctypes.c_int64, ctypes.c_double, _P, _P, _P, _P]),
     ("eik_sfs_forcing", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double, _P, _P]),
+    ("eik_fft_series", ctypes.c_int,
+     [ctypes.POINTER(ctypes.c_int64), ctypes.c_double, ctypes.c_double, _P, _P, ctypes.c_int64,
+      ctypes.c_int, ctypes.c_double, _P, _P, ctypes.POINTER(ctypes.c_double), _P]),
     ("eik_last_error", ctypes.c_char_p, []),
     ("eik_abi_version", ctypes.c_int, []),
     ("eik_cuda_arch", ctypes.c_int, []),

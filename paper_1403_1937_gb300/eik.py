@@ -419,6 +419,41 @@ def sfs_forcing(P, f_min: float = 0.0, stream=None):
     return f
 
 
+def fft_series(dims: Sequence[int], h: float, hbar: float, f, src_idx, terms: int,
+               f_tilde: float = 0.0, stream=None):
+    """FFT perturbation series (C: ``eik_fft_series``, Sec. 5 Table 1) on a
+    2D grid dims = (nx, ny); f and src_idx host arrays or CUDA tensors.
+    Returns (S, phi, f_tilde) with S and phi as CUDA float64 tensors (numpy
+    arrays without a GPU-resident input) of nx*ny values, x fastest."""
+    dims = tuple(int(d) for d in dims)
+    n = int(np.prod(dims))
+    if _numel(f) != n:
+        raise ValueError("f must have prod(dims) elements")
+    if not _is_torch(src_idx):
+        src_idx = np.ascontiguousarray(np.asarray(src_idx, dtype=np.int64).ravel())
+    device = _is_torch(f) and f.is_cuda
+    if device:
+        import torch
+        S = torch.empty(n, dtype=torch.float64, device=f.device)
+        phi = torch.empty(n, dtype=torch.float64, device=f.device)
+    else:
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        S = np.empty(n, dtype=np.float64)
+        phi = np.empty(n, dtype=np.float64)
+    fp, fk = _ptr(f, np.float64, "f")
+    sp, sk = _ptr(src_idx, np.int64, "src_idx")
+    Sp, Sk = _ptr(S, np.float64, "S")
+    pp, pk = _ptr(phi, np.float64, "phi")
+    d = (ctypes.c_int64 * 2)(*dims)
+    ft = ctypes.c_double()
+    st = _lib.load().eik_fft_series(d, float(h), float(hbar), fp, sp, _numel(src_idx),
+                                    int(terms), float(f_tilde), Sp, pp, ctypes.byref(ft),
+                                    _stream_ptr(stream))
+    if st != _lib.EIK_OK:
+        raise _lib.EikError(st, "eik_fft_series failed")
+    return S, phi, ft.value
+
+
 def solve(f, h: float, hbar: float, src_idx, src_U=None, precision: str = "fp64",
           tol: Optional[float] = None, want_phi: bool = False, **kw):
     """One-shot convenience: dims are taken from the array shape (numpy order

@@ -128,3 +128,28 @@ def test_path_and_forcing_entry_points_validate_arguments_without_gpu(lib):
                    (0.1, float("nan")), (-0.1, 0.1), (0.1, 0.0)):
         assert lib.eik_residual_noalloc(2, ok, hh, hb, P, P, P, 1, 0, res, None) == \
             _lib.EIK_ERR_ARG, (hh, hb)
+
+
+def test_fft_series_validates_arguments_without_gpu(lib):
+    """eik_fft_series rejects bad sizes, spacings, term counts and f~ before
+    any CUDA call."""
+    import math
+    from paper_1403_1937_gb300 import _lib
+    P = ctypes.c_void_p(0x1000)      # never dereferenced: the checks fail first
+    d = (ctypes.c_int64 * 2)(9, 7)
+    ft = ctypes.c_double()
+    for dims in ((1, 7), (9, 1), (4097, 8), (8, 4097)):
+        dd = (ctypes.c_int64 * 2)(*dims)
+        assert lib.eik_fft_series(dd, 0.1, 0.1, P, P, 1, 2, 0.0, P, None, ctypes.byref(ft),
+                                  None) == _lib.EIK_ERR_ARG, dims
+    for h, hb in ((0.0, 0.1), (0.1, -1.0), (math.inf, 0.1), (0.1, math.nan)):
+        assert lib.eik_fft_series(d, h, hb, P, P, 1, 2, 0.0, P, None, None, None) == \
+            _lib.EIK_ERR_ARG, (h, hb)
+    for terms, fti, nsrc in ((-1, 0.0, 1), (65, 0.0, 1), (2, -1.0, 1), (2, math.inf, 1),
+                             (2, 0.0, 0)):
+        assert lib.eik_fft_series(d, 0.1, 0.1, P, P, nsrc, terms, fti, P, None, None,
+                                  None) == _lib.EIK_ERR_ARG, (terms, fti, nsrc)
+    assert lib.eik_fft_series(d, 0.1, 0.1, None, P, 1, 2, 0.0, P, None, None, None) == \
+        _lib.EIK_ERR_ARG
+    assert lib.eik_fft_series(d, 0.1, 0.1, P, P, 1, 2, 0.0, None, None, None, None) == \
+        _lib.EIK_ERR_ARG

@@ -65,6 +65,7 @@ def test_recorded_traffic_matches_the_committed_kernels():
     """Every entry of profiles/traffic.json for the default kernels is keyed
     to the current source, so the bench reports it (not null)."""
     import bench
-    for key in ("cg_pass1_64@c2", "cg_pass2_64@c2", "mixed_cg@c2", "mixed_cg@c3"):
+    for key in ("cg_pass1_64@c2", "cg_pass2_64@c2", "mixed_cg@c2", "mixed_cg@c3",
+                "mixed_cg_packed@c4"):
         kernel, wl = key.split("@")
         assert bench.ncu_traffic(kernel, wl) is not None, key

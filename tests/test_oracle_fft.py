@@ -45,8 +45,7 @@ def test_constant_f_is_the_closed_form():
     ref = ref.reshape(-1)
     # the transforms carry absolute errors of about eps * max(phi) (the
     # paper's reason for MPFR at small hbar, Sec. 5, Numerical issues), so
-    # phi is exact to
-    # that level and S = -hbar log phi to hbar * that / phi
+    # phi is exact to that level and S = -hbar log phi to hbar * that / phi
     eta = 1e-14 * ref.max()
     assert np.max(np.abs(phi - ref)) <= eta
     assert np.all(np.abs(S + hbar * np.log(ref)) <= hbar * eta / ref + 1e-13)
