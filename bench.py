@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "fft"])
     ap.add_argument("--c4-count", type=int, default=256,
                     help="instances in the batched workload (c4)")
     ap.add_argument("--tol", type=float, default=None,
@@ -595,6 +595,76 @@ def run_batch(args):
         print(json.dumps(line), flush=True)
 
 
+def fft_flops(n, terms):
+    """FP64 operations of the 1D transforms eik_fft_series runs on an n x n
+    grid with `terms` terms, at the usual 5 N log2 N per complex transform of
+    length N: transform length P = the power of two >= 2n - 1; the kernels'
+    transforms (G~, and G when terms > 0) take 2P row transforms, a grid
+    function's forward transform n + P and its inverse P + n."""
+    P = 1
+    while P < 2 * n - 1:
+        P *= 2
+    per = 5 * P * np.log2(P)
+    kernels = 2 * P * (1 + (1 if terms > 0 else 0))
+    data = (1 + terms) * 2 * (n + P)
+    return float(per * (kernels + data))
+
+
+def run_fft(args):
+    """Second workload: the FFT perturbation series (Sec. 5, Table 1) on
+    Example 1 of Sec. 5.4 (257^2, hbar = 0.006, T = 6) and on the same
+    domain at 4x the resolution (1025^2, hbar scaled with h), timed with CUDA
+    events around eik_fft_series with device-resident inputs."""
+    import torch
+    from paper_1403_1937_gb300 import build as _build
+    if not _build.up_to_date():
+        _build.build()
+    from paper_1403_1937_gb300 import eik
+    from paper_1403_1937_gb300 import workloads as wl
+    torch.cuda.set_device(0)
+    rows = []
+    with Clocks(0) as clk:
+        for scale in (1, 4):
+            inst = wl.example1(h=2.0 ** -10 / scale, hbar=0.006 / scale)
+            n = inst.dims[0]
+            f = torch.from_numpy(inst.f).cuda()
+            for _ in range(args.warmup):
+                eik.fft_series(inst.dims, inst.h, inst.hbar, f, inst.src_idx, 6)
+            ts = []
+            for _ in range(args.steps):
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                eik.fft_series(inst.dims, inst.h, inst.hbar, f, inst.src_idx, 6)
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            ms = statistics.median(ts)
+            fl = fft_flops(n, 6)
+            rows.append({"grid": [n, n], "hbar": inst.hbar, "terms": 6, "ms": round(ms, 3),
+                         "transform_tflops": round(fl / (ms * 1e-3) / 1e12, 4)})
+    peak = FP64_PEAK_TFLOPS
+    line = {"metric": "FFT perturbation series (Sec. 5, Table 1): time per evaluation",
+            "value": rows[0]["ms"], "unit": "ms", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": rows[0]["ms"], "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "Sec. 5.4 Example 1: f = exp(r) on [-0.125, 0.125]^2, "
+                                   "one source at the origin, 6 terms",
+                       "grids": rows},
+            "roofline": {"bound": "fp64", "kernel": "k_fft_rows (all transforms)",
+                         "achieved": rows[-1]["transform_tflops"], "peak": peak,
+                         "unit": "TFLOP/s",
+                         "frac": round(rows[-1]["transform_tflops"] / peak, 4),
+                         "traffic": None, "peak_source": "nominal FP64 rate (no measured "
+                                                         "FP64 peak on this pool)",
+                         "note": "5 N log2 N per transform over the whole call (pointwise "
+                                 "kernels and the Green's function samples included in the "
+                                 "time)"},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def roofline(res, inst, wname):
     peak, peak_src = measured_peaks()
     km = {k: v for k, v in res["kernel_ms"].items() if v[0] is not None}
@@ -683,6 +753,9 @@ def main():
         return
     if args.workload == "c5":
         run_diff(args)
+        return
+    if args.workload == "fft":
+        run_fft(args)
         return
     inst, desc, n_unk, results, ws, rank = run_ours(args)
     c3 = None

@@ -469,7 +469,7 @@ eik_status batch_exec_create(BatchExec **out, int count, const int *nx, const in
   ok = ok && cudaMalloc((void **)&e->cnt, sizeof(unsigned) * count) == cudaSuccess;
   ok = ok && cudaMalloc((void **)&e->row_inst, sizeof(int) * e->H) == cudaSuccess;
   ok = ok && cudaMalloc((void **)&e->bc, sizeof(BatchCtl)) == cudaSuccess;
-  ok = ok && cudaMalloc((void **)&e->part, sizeof(double) * 5 * (size_t)cap) == cudaSuccess;
+  ok = ok && cudaMalloc((void **)&e->part, sizeof(double) * 6 * (size_t)cap) == cudaSuccess;
   ok = ok && cudaMalloc((void **)&e->alive, sizeof(int) * count) == cudaSuccess;
   ok = ok && cudaEventCreate(&e->ev[0]) == cudaSuccess && cudaEventCreate(&e->ev[1]) == cudaSuccess;
   ok = ok && cudaMallocHost((void **)&e->h_bc, sizeof(BatchCtl)) == cudaSuccess;

@@ -46,23 +46,24 @@ __device__ __forceinline__ double acc_ratio(const Acc &a, const Acc &b) {
 
 // --------------------------------------------------------------- pass tail
 __device__ void cg_update(MixCtl *st, double G, double D, double R, double P, double Bd,
-                          bool INIT);
+                          double PS, bool INIT);
 
-// Per-block partials: <r,r> and <w,r> (both in units of 2^(2F + fd)), the
+// Per-block partials: <r,r>, <w,r> and <p,Ap> (units of 2^(2F + fd)), the
 // largest |r| and |p| (frame units), and the componentwise-test flag.  The
 // last block forms the next alpha, beta, frame and the stopping decision.
 template <bool INIT>
-__device__ void cg_tail(float gam, float dlt, float rmax, float pmax, int bad, bool fault,
-                        MixCtl *st, double *part, int nblk_part) {
+__device__ void cg_tail(float gam, float dlt, float rmax, float pmax, int bad, float pap,
+                        bool fault, MixCtl *st, double *part, int nblk_part) {
   __shared__ int flag;
   for (int o = 16; o > 0; o >>= 1) {
     gam += __shfl_down_sync(0xffffffffu, gam, o);
     dlt += __shfl_down_sync(0xffffffffu, dlt, o);
+    pap += __shfl_down_sync(0xffffffffu, pap, o);
     rmax = fmaxf(rmax, __shfl_down_sync(0xffffffffu, rmax, o));
     pmax = fmaxf(pmax, __shfl_down_sync(0xffffffffu, pmax, o));
     bad |= __shfl_down_sync(0xffffffffu, bad, o);
   }
-  __shared__ float wg[32], wd[32], wr[32], wp[32];
+  __shared__ float wg[32], wd[32], wr[32], wp[32], wq[32];
   __shared__ int wb[32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   if (lane == 0) {
@@ -71,15 +72,17 @@ __device__ void cg_tail(float gam, float dlt, float rmax, float pmax, int bad, b
     wr[w] = rmax;
     wp[w] = pmax;
     wb[w] = bad;
+    wq[w] = pap;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double G = 0.0, D = 0.0;
+    double G = 0.0, D = 0.0, Q = 0.0;
     float R = 0.f, P = 0.f;
     int Bd = 0;
     for (int k = 0; k < nwarp; ++k) {
       G += (double)wg[k];
       D += (double)wd[k];
+      Q += (double)wq[k];
       R = fmaxf(R, wr[k]);
       P = fmaxf(P, wp[k]);
       Bd |= wb[k];
@@ -89,18 +92,20 @@ __device__ void cg_tail(float gam, float dlt, float rmax, float pmax, int bad, b
     part[2 * nblk_part + blockIdx.x] = (double)R;
     part[3 * nblk_part + blockIdx.x] = (double)P;
     part[4 * nblk_part + blockIdx.x] = (double)Bd;
+    part[5 * nblk_part + blockIdx.x] = Q;
     if (fault) atomicExch(&st->fault, 1);
   }
   if (!last_block(&st->counter[1], &flag)) return;
-  // the five partial arrays in one round: every load is issued before any
-  // is used, then one shuffle tree and one shared-memory step per quantity
-  double G = 0.0, D = 0.0, R = 0.0, P = 0.0, Bd = 0.0;
+  // the six partial arrays in one round: every load is issued before any is
+  // used, then one shuffle tree and one shared-memory step per quantity
+  double G = 0.0, D = 0.0, R = 0.0, P = 0.0, Bd = 0.0, Q = 0.0;
   for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
     const double g0 = __ldcg(part + b), d0 = __ldcg(part + nblk_part + b);
     const double r0 = __ldcg(part + 2 * nblk_part + b), p0 = __ldcg(part + 3 * nblk_part + b);
-    const double b0 = __ldcg(part + 4 * nblk_part + b);
+    const double b0 = __ldcg(part + 4 * nblk_part + b), q0 = __ldcg(part + 5 * nblk_part + b);
     G += g0;
     D += d0;
+    Q += q0;
     R = fmax(R, r0);
     P = fmax(P, p0);
     Bd = fmax(Bd, b0);
@@ -108,42 +113,46 @@ __device__ void cg_tail(float gam, float dlt, float rmax, float pmax, int bad, b
   for (int o = 16; o > 0; o >>= 1) {
     G += __shfl_down_sync(0xffffffffu, G, o);
     D += __shfl_down_sync(0xffffffffu, D, o);
+    Q += __shfl_down_sync(0xffffffffu, Q, o);
     R = fmax(R, __shfl_down_sync(0xffffffffu, R, o));
     P = fmax(P, __shfl_down_sync(0xffffffffu, P, o));
     Bd = fmax(Bd, __shfl_down_sync(0xffffffffu, Bd, o));
   }
-  __shared__ double tg[32], td[32], tr[32], tp[32], tb[32];
+  __shared__ double tg[32], td[32], tr[32], tp[32], tb[32], tq[32];
   if (lane == 0) {
     tg[w] = G;
     td[w] = D;
     tr[w] = R;
     tp[w] = P;
     tb[w] = Bd;
+    tq[w] = Q;
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
   G = 0.0;
   D = 0.0;
+  Q = 0.0;
   R = 0.0;
   P = 0.0;
   Bd = 0.0;
   for (int k = 0; k < nwarp; ++k) {   // fixed order: deterministic
     G += tg[k];
     D += td[k];
+    Q += tq[k];
     R = fmax(R, tr[k]);
     P = fmax(P, tp[k]);
     Bd = fmax(Bd, tb[k]);
   }
   st->counter[1] = 0u;
-  cg_update(st, G, D, R, P, Bd, INIT);
+  cg_update(st, G, D, R, P, Bd, Q, INIT);
 }
 
 // The recurrence step of one inner solve from the pass's totals: G = <r,r>,
-// D = <w,r> (units 2^(2F + fd)), R = max|r|, P = max|p| (frame units), Bd the
-// componentwise-test flag.  INIT: the solve's first pass (w = A r).  Run by
-// one thread.
+// D = <w,r>, PS = <p,Ap> of this pass's direction (units 2^(2F + fd)),
+// R = max|r|, P = max|p| (frame units), Bd the componentwise-test flag.
+// INIT: the solve's first pass (w = A r).  Run by one thread.
 __device__ void cg_update(MixCtl *st, double G, double D, double R, double P, double Bd,
-                          bool INIT) {
+                          double PS, bool INIT) {
   const int F = st->F, dF = st->dF, fd = st->fd;
   const Acc gam_new = acc_of(G, 2 * F + fd);
   const Acc dlt_new = acc_of(D, 2 * F + fd);
@@ -157,7 +166,7 @@ __device__ void cg_update(MixCtl *st, double G, double D, double R, double P, do
     st->status = EIK_ERR_TIMEOUT;
     return;
   }
-  if (!isfinite(G) || !isfinite(D) || !isfinite(R) || !isfinite(P)) {
+  if (!isfinite(G) || !isfinite(D) || !isfinite(R) || !isfinite(P) || !isfinite(PS)) {
     st->done = 1;
     st->status = EIK_ERR_BREAKDOWN;
     return;
@@ -182,8 +191,13 @@ __device__ void cg_update(MixCtl *st, double G, double D, double R, double P, do
     st->beta = 0.0;
   } else {
     const double beta_new = acc_ratio(gam_new, gam_old);
-    const double den = acc_ratio(dlt_new, gam_new) - beta_new / st->alpha;
-    alpha_new = (den > 0.0 && isfinite(den)) ? 1.0 / den : -1.0;
+    // <p', A p'> of the next direction p' = r + beta p is <w, r> - beta^2
+    // <p, A p> (CG's orthogonality), with <p, A p> of this pass's direction
+    // summed in the pass itself: the single-reduction recurrence would carry
+    // it as <r,r>_old / alpha_old instead, and in FP32 that chain loses the
+    // positive definiteness on badly conditioned operators
+    const double pap = D - beta_new * beta_new * PS;
+    alpha_new = (PS > 0.0 && pap > 0.0 && isfinite(pap)) ? G / pap : -1.0;
     st->beta = beta_new;
   }
   if (!(alpha_new > 0.0) || !isfinite(alpha_new)) {
@@ -292,7 +306,7 @@ __device__ __forceinline__ float4 mul4(const float4 &a, const float4 &b) {
 }
 
 template <bool INIT, int NS, int WPB>
-__global__ void __launch_bounds__(32 * WPB)
+__global__ void __launch_bounds__(32 * WPB, WPB >= 7 ? 2 : 3)
 k_cg2d(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtensorMap tm_p,
        const __grid_constant__ CUtensorMap tm_s, Grid g, CellGrid cg,
        const int *__restrict__ kx, int tiles_x, int TY, int ntiles,
@@ -361,7 +375,7 @@ k_cg2d(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtenso
   }
   __syncwarp();
 
-  float gam = 0.f, dlt = 0.f, rmax = 0.f, pmax = 0.f;
+  float gam = 0.f, dlt = 0.f, rmax = 0.f, pmax = 0.f, pap = 0.f;
   int bad = 0;
   bool fault = false;
   int q = 0;
@@ -448,6 +462,7 @@ k_cg2d(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtenso
         const float4 r4 = ld4(S1 + OR + c), s4 = ld4(S1 + OS + c);
         float rn[4];
         const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
+        float ps = 0.f;   // sum of p (A p) over the lane's nodes of this row
         if (INIT) {
           rn[0] = r4.x; rn[1] = r4.y; rn[2] = r4.z; rn[3] = r4.w;
         } else {
@@ -465,9 +480,13 @@ k_cg2d(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtenso
           for (int i = 0; i < 4; ++i) {
             const float ys = fmaf(ysP[i], fb.fP, ysN[i] * fb.fN);
             const float acc = fmaf(hy1, xs[i], hx[i] * ys);
-            rn[i] = fmaf(-alpha, fmaf(-sv[i], acc, pv[i]), rv[i]);
+            const float si = fmaf(-sv[i], acc, pv[i]);   // (A p)_i
+            rn[i] = fmaf(-alpha, si, rv[i]);
+            ps = fmaf(pv[i], si, ps);
           }
         }
+        // <p, A p> over the tile's own rows (the halo rows belong to others)
+        if (j >= 3 && j <= TY + 2 && y1 < g.ny) pap = fmaf(ps, fb.W, pap);
         st4(RB + c, rn[0], rn[1], rn[2], rn[3]);
         st4(RB + kWin + c, sv[0] * rn[0], sv[1] * rn[1], sv[2] * rn[2], sv[3] * rn[3]);
         if (l0 || l31) {
@@ -553,7 +572,7 @@ k_cg2d(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtenso
       if (!(qq == 0 && withhold)) mbar_wait_bounded(&bar[qq % NS], (uint32_t)(qq / NS) & 1u);
   }
   __syncwarp();
-  cg_tail<INIT>(gam, dlt, rmax, pmax, bad, fault, st, part, nblk_part);
+  cg_tail<INIT>(gam, dlt, rmax, pmax, bad, pap, fault, st, part, nblk_part);
 }
 
 // ------------------------------------------------------- packed 2D batch
@@ -593,16 +612,18 @@ __device__ __forceinline__ int batch_find(const int *pre, int m, int t) {
   return lo;
 }
 
-// End of one tile: its partials, and the instance's recurrence step when this
-// was the instance's last tile of the pass.  Whole warp.
-__device__ void batch_tile_done(float gam, float dlt, float rmax, float pmax, int bad, int t,
-                                int inst, int a, const int *pre, MixCtl *st, unsigned *cnt,
-                                int *alive, BatchCtl *bc, double *part, int cap,
+// End of one tile: its six partials (as cg_tail's), and the instance's
+// recurrence step when this was the instance's last tile of the pass.  Whole
+// warp.
+__device__ void batch_tile_done(float gam, float dlt, float rmax, float pmax, int bad,
+                                float pap, int t, int inst, int a, const int *pre, MixCtl *st,
+                                unsigned *cnt, int *alive, BatchCtl *bc, double *part, int cap,
                                 BatchDone *done) {
   const int lane = threadIdx.x & 31;
   for (int o = 16; o > 0; o >>= 1) {
     gam += __shfl_down_sync(0xffffffffu, gam, o);
     dlt += __shfl_down_sync(0xffffffffu, dlt, o);
+    pap += __shfl_down_sync(0xffffffffu, pap, o);
     rmax = fmaxf(rmax, __shfl_down_sync(0xffffffffu, rmax, o));
     pmax = fmaxf(pmax, __shfl_down_sync(0xffffffffu, pmax, o));
     bad |= __shfl_down_sync(0xffffffffu, bad, o);
@@ -615,23 +636,26 @@ __device__ void batch_tile_done(float gam, float dlt, float rmax, float pmax, in
     part[2 * cap + t] = (double)rmax;
     part[3 * cap + t] = (double)pmax;
     part[4 * cap + t] = (double)bad;
+    part[5 * cap + t] = (double)pap;
     __threadfence();
     last = atomicAdd(&cnt[inst], 1u) == (unsigned)(p1 - p0 - 1);
   }
   last = __shfl_sync(0xffffffffu, last, 0);
   if (!last) return;
   __threadfence();
-  double G = 0.0, D = 0.0, R = 0.0, P = 0.0, Bd = 0.0;
+  double G = 0.0, D = 0.0, R = 0.0, P = 0.0, Bd = 0.0, Q = 0.0;
   for (int u = p0 + lane; u < p1; u += 32) {
     G += __ldcg(part + u);
     D += __ldcg(part + cap + u);
     R = fmax(R, __ldcg(part + 2 * cap + u));
     P = fmax(P, __ldcg(part + 3 * cap + u));
     Bd = fmax(Bd, __ldcg(part + 4 * cap + u));
+    Q += __ldcg(part + 5 * cap + u);
   }
   for (int o = 16; o > 0; o >>= 1) {   // fixed tree: deterministic
     G += __shfl_down_sync(0xffffffffu, G, o);
     D += __shfl_down_sync(0xffffffffu, D, o);
+    Q += __shfl_down_sync(0xffffffffu, Q, o);
     R = fmax(R, __shfl_down_sync(0xffffffffu, R, o));
     P = fmax(P, __shfl_down_sync(0xffffffffu, P, o));
     Bd = fmax(Bd, __shfl_down_sync(0xffffffffu, Bd, o));
@@ -641,7 +665,7 @@ __device__ void batch_tile_done(float gam, float dlt, float rmax, float pmax, in
     MixCtl *S = st + inst;
     const bool init = S->first != 0;
     S->first = 0;
-    cg_update(S, G, D, R, P, Bd, init);
+    cg_update(S, G, D, R, P, Bd, Q, init);
     if (S->done) {
       alive[inst] = 0;
       BatchDone *h = done + inst;
@@ -864,7 +888,7 @@ k_cg2d_batch(const __grid_constant__ CUtensorMap tm_r0, const __grid_constant__ 
         kt = KTab{tab, cr0, cc0, ncol};
       }
     }
-    float gam = 0.f, dlt = 0.f, rmax = 0.f, pmax = 0.f;
+    float gam = 0.f, dlt = 0.f, rmax = 0.f, pmax = 0.f, pap = 0.f;
     int bad = 0;
     float4 dq0 = make_float4(0, 0, 0, 0), dq1 = dq0, dq2 = dq0;
     float4 xq0 = dq0, xq1 = dq0, xq2 = dq0;
@@ -906,6 +930,7 @@ k_cg2d_batch(const __grid_constant__ CUtensorMap tm_r0, const __grid_constant__ 
         const float4 r4 = ld4(S1 + OR + c), s4 = ld4(S1 + OS + c);
         float rn[4];
         const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
+        float ps = 0.f;   // sum of p (A p) over the lane's nodes of this row
         {
           fac2_update(fb, y1, dir, g, cg, kx, kt, cxo, cxl, cxr, cxh, fd);
           const float4 p4 = ld4(S1 + OP + c);
@@ -921,9 +946,13 @@ k_cg2d_batch(const __grid_constant__ CUtensorMap tm_r0, const __grid_constant__ 
           for (int i = 0; i < 4; ++i) {
             const float ys = fmaf(ysP[i], fb.fP, ysN[i] * fb.fN);
             const float acc = fmaf(hy1, xs[i], hx[i] * ys);
-            rn[i] = fmaf(-alpha, fmaf(-sv[i], acc, pv[i]), rv[i]);
+            const float si = fmaf(-sv[i], acc, pv[i]);   // (A p)_i
+            rn[i] = fmaf(-alpha, si, rv[i]);
+            ps = fmaf(pv[i], si, ps);
           }
         }
+        // <p, A p> over the tile's own rows (the halo rows belong to others)
+        if (j >= 3 && j <= TY + 2 && y1 < g.ny) pap = fmaf(ps, fb.W, pap);
         st4(RB + c, rn[0], rn[1], rn[2], rn[3]);
         st4(RB + kWin + c, sv[0] * rn[0], sv[1] * rn[1], sv[2] * rn[2], sv[3] * rn[3]);
         if (l0 || l31) {
@@ -994,7 +1023,7 @@ k_cg2d_batch(const __grid_constant__ CUtensorMap tm_r0, const __grid_constant__ 
       }
     }
     if (fault) break;
-    batch_tile_done(gam, dlt, rmax, pmax, bad, t, inst, a, pre, st, cnt, alive, bc, part,
+    batch_tile_done(gam, dlt, rmax, pmax, bad, pap, t, inst, a, pre, st, cnt, alive, bc, part,
                     part_cap, done);
   }
   if (fault && l0) {
@@ -1117,7 +1146,8 @@ k_cg3d(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtenso
   const int hI = l31 ? hB - 1 : hB + 1;       // its neighbour inside the tile
   const int hO = l31 ? hB + 1 : hB - 1;       // and outside
   const int rw = w * kWin;                    // the warp's row in a plane
-  float gam = 0.f, dlt = 0.f, rmax = 0.f, pmax = 0.f;
+  float gam = 0.f, dlt = 0.f, rmax = 0.f, pmax = 0.f, pap = 0.f;
+  float psb = 0.f, psc = 0.f;   // p (A p) of B's row this step / the step before
   int bad = 0;
   bool fault = false;
   int q = 0;
@@ -1197,6 +1227,7 @@ k_cg3d(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtenso
         const float4 r4 = ld4(S1 + rw + c), s4 = ld4(S1 + 2 * PLANE + rw + c);
         float rn[4];
         const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
+        float ps = 0.f;   // sum of p (A p) over the lane's nodes of this row
         float hrn = S1[rw + hB];
         const float hs = S1[2 * PLANE + rw + hB];
         if (INIT) {
@@ -1239,7 +1270,9 @@ k_cg3d(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtenso
             const float ys = fmaf(ysS[i], bS, ysN[i] * bN);
             const float zs = fmaf(zsP[i], bP, zsN[i] * bNz);
             const float acc = fmaf(wxe, xs[i], hx[i] * fmaf(hz1, ys, hy * zs));
-            rn[i] = fmaf(-alpha, fmaf(-sv[i], acc, pv[i]), rv[i]);
+            const float si = fmaf(-sv[i], acc, pv[i]);   // (A p)_i
+            rn[i] = fmaf(-alpha, si, rv[i]);
+            ps = fmaf(pv[i], si, ps);
           }
           if (l0 || l31) {
             const float uin = S1[2 * PLANE + rw + hI] * S1[PLANE + rw + hI];
@@ -1259,6 +1292,7 @@ k_cg3d(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtenso
           *reinterpret_cast<float4 *>(RC + PLANE + rw + c) = s4;
           if (!INIT) *reinterpret_cast<float4 *>(RC + 2 * PLANE + rw + c) = ld4(S1 + PLANE + rw + c);
         }
+        psb = ps;
       }
       // ---- C: plane z_{j-2} (B wrote its neighbours' un in earlier steps,
       // and this warp's own un of plane z_{j-1} just now)
@@ -1316,6 +1350,7 @@ k_cg3d(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtenso
             pmax = fmaxf(pmax, fabsf(pv[i]));
             if (check && fabsf(rv[i]) > thetaF * fabsf(xv[i] + dn[i])) bad = 1;
           }
+          pap = fmaf(psc, cW, pap);
           if (!INIT && st_ok) {
             const int64_t o = ((int64_t)z2 * g.ny + y) * px + xl;
             st4(d + o, dn[0], dn[1], dn[2], dn[3]);
@@ -1324,6 +1359,7 @@ k_cg3d(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtenso
           }
         }
       }
+      psc = psb;
       dq2 = dq1;
       dq1 = dq0;
       xq2 = xq1;
@@ -1344,7 +1380,7 @@ k_cg3d(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtenso
         if (!(qq == 0 && withhold)) mbar_wait_bounded(&bars[qq % NS], (uint32_t)(qq / NS) & 1u);
     __syncthreads();
   }
-  cg_tail<INIT>(gam, dlt, rmax, pmax, bad, fault, st, part, nblk_part);
+  cg_tail<INIT>(gam, dlt, rmax, pmax, bad, pap, fault, st, part, nblk_part);
 }
 
 // ------------------------------------------------------------------ host

@@ -14,9 +14,13 @@
 // The iteration is the single-reduction ("Chronopoulos-Gear") form of CG:
 // one pass over the grid per iteration computes
 //   p = r + beta p,  s = A p,  d += alpha p,  r -= alpha s,  w = A r,
-// and the two inner products <r, r> and <w, r>, from which the last block
+// and the inner products <r, r>, <w, r> and <p, s>, from which the last block
 // forms the next beta = <r,r>_new / <r,r>_old and
-//   alpha = <r,r>_new / (<w,r>_new - beta <r,r>_new / alpha_old).
+//   alpha = <r,r>_new / (<w,r>_new - beta^2 <p, s>),
+// the denominator being <p', A p'> of the next direction.  (The textbook
+// form carries <p, A p> as <r,r>_old / alpha_old instead; summing it in the
+// pass keeps the FP32 recurrence from drifting on badly conditioned
+// operators.)
 // A pass recomputes s = A p instead of storing it, so it reads r and p with a
 // two-node halo, sigma, d (and, in checking passes, the FP32 copy of the
 // iterate) and writes r, p and d: 7 words per node.
@@ -175,7 +179,7 @@ struct Cg32BatchBuffers {
   unsigned *cnt;         // per-instance tile tickets of the current pass
   int *alive;            // 1 while an instance is in the list and iterating
   BatchCtl *bc;
-  double *part;          // 5 x part_cap per-tile partials
+  double *part;          // 6 x part_cap per-tile partials
   int part_cap;
   BatchRing *ring;       // device view of the mapped request ring
   int ring_cap;

@@ -129,23 +129,39 @@ __device__ __forceinline__ bool wrapped(int i, int P, int n, int *o) {
   return false;
 }
 
-// Kernel sampled at the wrapped offsets into a (Py x Px, pitch Px) complex
-// array: mode 0 G~ = exp(-f~ r / hbar); mode 1 G (origin: *g0).
-__global__ void k_fill_kernel(double2 *a, int Px, int Py, int nx, int ny, double h, double ft,
-                              double hbar, int mode, const double *g0) {
-  const int64_t tot = (int64_t)Px * Py;
+// G at the offsets 0 <= b <= a < m, packed as tab[a (a + 1) / 2 + b] (G
+// depends on |offset| only, so one octant serves all); the origin takes *g0.
+__global__ void k_green_table(double *tab, int m, double h, double ft, double hbar,
+                              const double *g0) {
+  const int64_t tot = (int64_t)m * (m + 1) / 2;
   const double inv2pi = 1.0 / (2.0 * M_PI * hbar * hbar);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int a = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
+    while ((int64_t)a * (a + 1) / 2 > e) --a;
+    while ((int64_t)(a + 1) * (a + 2) / 2 <= e) ++a;
+    const int b = (int)(e - (int64_t)a * (a + 1) / 2);
+    tab[e] = (a == 0) ? *g0 : bessel_k(0, ft * h * hypot((double)a, (double)b) / hbar) * inv2pi;
+  }
+}
+
+// Kernel sampled at the wrapped offsets into a (Py x Px, pitch Px) complex
+// array: mode 0 G~ = exp(-f~ r / hbar); mode 1 G from the octant table.
+__global__ void k_fill_kernel(double2 *a, int Px, int Py, int nx, int ny, double h, double ft,
+                              double hbar, int mode, const double *__restrict__ tab) {
+  const int64_t tot = (int64_t)Px * Py;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int ix = (int)(e % Px), iy = (int)(e / Px);
     int ox, oy;
     double v = 0.0;
     if (wrapped(ix, Px, nx, &ox) && wrapped(iy, Py, ny, &oy)) {
-      const double r = h * hypot((double)ox, (double)oy);
-      if (mode == 0)
-        v = exp(-ft * r / hbar);
-      else
-        v = (ox == 0 && oy == 0) ? *g0 : bessel_k(0, ft * r / hbar) * inv2pi;
+      if (mode == 0) {
+        v = exp(-ft * h * hypot((double)ox, (double)oy) / hbar);
+      } else {
+        const int p = max(abs(ox), abs(oy)), q = min(abs(ox), abs(oy));
+        v = tab[(int64_t)p * (p + 1) / 2 + q];
+      }
     }
     a[e] = make_double2(v, 0.0);
   }
@@ -279,18 +295,21 @@ void transpose(const Fft2 &F, const double2 *in, double2 *out, int r, int c) {
   k_transpose<<<g, b, 0, F.s>>>(in, out, r, c);
 }
 
-// A (grid layout) -> B (spectrum, transposed layout)
-void forward(const Fft2 &F) {
-  rows(F, F.A, F.Py, F.Px, F.lgx, F.twx, false);
+// A (grid layout) -> B (spectrum, transposed layout).  Rows of A at and past
+// `rows_in` are zero (grid functions), so their transforms are zero and are
+// skipped.
+void forward(const Fft2 &F, int rows_in) {
+  rows(F, F.A, rows_in, F.Px, F.lgx, F.twx, false);
   transpose(F, F.A, F.B, F.Py, F.Px);
   rows(F, F.B, F.Px, F.Py, F.lgy, F.twy, false);
 }
 
-// B (spectrum) -> A (grid layout), unscaled
-void inverse(const Fft2 &F) {
+// B (spectrum) -> A (grid layout), unscaled; only the first `rows_out` rows
+// of A (the grid's) are transformed back.
+void inverse(const Fft2 &F, int rows_out) {
   rows(F, F.B, F.Px, F.Py, F.lgy, F.twy, true);
   transpose(F, F.B, F.A, F.Px, F.Py);
-  rows(F, F.A, F.Py, F.Px, F.lgx, F.twx, true);
+  rows(F, F.A, rows_out, F.Px, F.lgx, F.twx, true);
 }
 
 struct Buf {
@@ -342,12 +361,15 @@ extern "C" eik_status eik_fft_series(const int64_t *dims, double h, double hbar,
   Buf buf;
   double2 *K = nullptr;
   double *fd = nullptr, *phi = nullptr, *t0 = nullptr, *t1 = nullptr, *mm = nullptr, *g0 = nullptr;
+  double *gtab = nullptr;
+  const int m = std::max(nx, ny);
   int64_t *src = nullptr;
   int *bad = nullptr;
   if (!buf.get(&F.twx, F.Px / 2) || !buf.get(&F.twy, F.Py / 2) || !buf.get(&F.A, np) ||
       !buf.get(&F.B, np) || !buf.get(&K, np) || !buf.get(&fd, n) || !buf.get(&phi, n) ||
       !buf.get(&t0, n) || !buf.get(&t1, n) || !buf.get(&mm, 2) || !buf.get(&g0, 1) ||
-      !buf.get(&src, nsrc) || !buf.get(&bad, 1)) {
+      !buf.get(&src, nsrc) || !buf.get(&bad, 1) ||
+      !buf.get(&gtab, (size_t)m * (m + 1) / 2)) {
     cudaGetLastError();
     return EIK_ERR_OOM;
   }
@@ -382,30 +404,31 @@ extern "C" eik_status eik_fft_series(const int64_t *dims, double h, double hbar,
   k_twiddles<<<(F.Py / 2 + 255) / 256, 256, 0, s>>>(F.twy, F.Py);
   const double inv = 1.0 / ((double)F.Px * F.Py);
   // Table 1 steps 1-5: phi_0 = G~ * delta_kron
-  k_fill_kernel<<<nb, kThreads, 0, s>>>(F.A, F.Px, F.Py, nx, ny, h, ft, hbar, 0, g0);
-  forward(F);
+  k_fill_kernel<<<nb, kThreads, 0, s>>>(F.A, F.Px, F.Py, nx, ny, h, ft, hbar, 0, gtab);
+  forward(F, F.Py);
   cudaMemcpyAsync(K, F.B, sizeof(double2) * np, cudaMemcpyDeviceToDevice, s);
   cudaMemsetAsync(F.A, 0, sizeof(double2) * np, s);
   k_delta<<<(int)((nsrc + 255) / 256), 256, 0, s>>>(F.A, F.Px, src, nsrc, nx);
-  forward(F);
+  forward(F, ny);
   k_cmul<<<nb, kThreads, 0, s>>>(F.B, K, np);
-  inverse(F);
+  inverse(F, ny);
   // step 6: phi = phi_0 (t0 holds phi_{i-1})
   k_extract<<<nb, kThreads, 0, s>>>(F.A, F.Px, nx, n, inv, 1.0, t0, phi, 1);
   // step 7: transform of G
   if (terms > 0) {
     k_cell_average<<<1, 256, 0, s>>>(h, ft, hbar, g0);
-    k_fill_kernel<<<nb, kThreads, 0, s>>>(F.A, F.Px, F.Py, nx, ny, h, ft, hbar, 1, g0);
-    forward(F);
+    k_green_table<<<nb, kThreads, 0, s>>>(gtab, m, h, ft, hbar, g0);
+    k_fill_kernel<<<nb, kThreads, 0, s>>>(F.A, F.Px, F.Py, nx, ny, h, ft, hbar, 1, gtab);
+    forward(F, F.Py);
     cudaMemcpyAsync(K, F.B, sizeof(double2) * np, cudaMemcpyDeviceToDevice, s);
   }
   // steps 8-14
   double *prev = t0, *cur = t1;
   for (int i = 1; i <= terms; ++i) {
     k_embed<<<nb, kThreads, 0, s>>>(F.A, F.Px, F.Py, nx, ny, fd, ft * ft, prev);
-    forward(F);
+    forward(F, ny);
     k_cmul<<<nb, kThreads, 0, s>>>(F.B, K, np);
-    inverse(F);
+    inverse(F, ny);
     k_extract<<<nb, kThreads, 0, s>>>(F.A, F.Px, nx, n, inv * h * h, (i & 1) ? -1.0 : 1.0, cur,
                                       phi, 0);
     std::swap(prev, cur);
