@@ -846,8 +846,7 @@ k_cg2d_batch(const __grid_constant__ CUtensorMap tm_r0, const __grid_constant__ 
     const bool check = S->mode != 0 && ((S->iter & 3) == 3);
     const float thetaF = (float)scalbn((double)S->theta, -F);
     const bool half = B.boundary == EIK_BOUNDARY_HALF_CELL;
-    float *r_out = (set ^ S->flip) ? r0 : r1;   // the other buffer set
-    float *p_out = (set ^ S->flip) ? p0 : p1;
+    const int wset = 1 - (set ^ S->flip);   // the other buffer set (written)
     Grid g{};
     g.nx = B.nx;
     g.ny = B.ny;
@@ -1007,8 +1006,8 @@ k_cg2d_batch(const __grid_constant__ CUtensorMap tm_r0, const __grid_constant__ 
           if (st_ok) {
             const int64_t o = rowoff + (int64_t)y2 * P + xl;
             st4(d + o, dn[0], dn[1], dn[2], dn[3]);
-            st4(r_out + o, rv[0] * gwr, rv[1] * gwr, rv[2] * gwr, rv[3] * gwr);
-            st4(p_out + o, pv[0] * gwr, pv[1] * gwr, pv[2] * gwr, pv[3] * gwr);
+            st4((wset ? r1 : r0) + o, rv[0] * gwr, rv[1] * gwr, rv[2] * gwr, rv[3] * gwr);
+            st4((wset ? p1 : p0) + o, pv[0] * gwr, pv[1] * gwr, pv[2] * gwr, pv[3] * gwr);
           }
         }
       }

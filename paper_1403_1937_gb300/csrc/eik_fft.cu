@@ -170,7 +170,8 @@ __global__ void k_fill_kernel(double2 *a, int Px, int Py, int nx, int ny, double
 // G's average over the cell [-h/2, h/2]^2: 8 rays' triangles, along each
 // int_0^R r K_0(a r) dr = (1 - a R K_1(a R)) / a^2, R = (h/2) / cos(theta),
 // over theta in [0, pi/4] by Simpson's rule (one block).
-__global__ void k_cell_average(double h, double ft, double hbar, double *g0) {
+__global__ void __launch_bounds__(1024)
+k_cell_average(double h, double ft, double hbar, double *g0) {
   constexpr int M = 2048;   // Simpson intervals (even)
   __shared__ double red[32];
   const double a = ft / hbar;
@@ -416,7 +417,7 @@ extern "C" eik_status eik_fft_series(const int64_t *dims, double h, double hbar,
   k_extract<<<nb, kThreads, 0, s>>>(F.A, F.Px, nx, n, inv, 1.0, t0, phi, 1);
   // step 7: transform of G
   if (terms > 0) {
-    k_cell_average<<<1, 256, 0, s>>>(h, ft, hbar, g0);
+    k_cell_average<<<1, 1024, 0, s>>>(h, ft, hbar, g0);
     k_green_table<<<nb, kThreads, 0, s>>>(gtab, m, h, ft, hbar, g0);
     k_fill_kernel<<<nb, kThreads, 0, s>>>(F.A, F.Px, F.Py, nx, ny, h, ft, hbar, 1, gtab);
     forward(F, F.Py);
