@@ -411,7 +411,7 @@ void exec_main(BatchExec *e) {
   const eik_status s = exec_run(e);
   if (s != EIK_OK) {
     e->exec_status = s;
-    e->abort.store(1);
+    e->abort.store(1, std::memory_order_release);
   }
 }
 
@@ -600,10 +600,10 @@ eik_status batch_exec_inner(BatchExec *e, int i, int seq, MixCtl *out) {
   e->cv.notify_all();
   volatile BatchDone *d = e->done + i;
   for (int spin = 0; d->done_seq != seq; ++spin) {
-    if (e->abort.load()) {
-      e->msg = e->msg.empty() ? "packed batch executor stopped" : e->msg;
+    // the executor wrote its status and message before raising abort, and
+    // writes neither afterwards
+    if (e->abort.load(std::memory_order_acquire))
       return e->exec_status != EIK_OK ? e->exec_status : EIK_ERR_CUDA;
-    }
     if (spin > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
   }
   std::atomic_thread_fence(std::memory_order_acquire);
@@ -646,6 +646,8 @@ void batch_exec_work(const BatchExec *e, int64_t *node_passes, double *ms) {
   *ms = e->pass_ms;
 }
 
-std::string batch_exec_error(const BatchExec *e) { return e->msg; }
+std::string batch_exec_error(const BatchExec *e) {
+  return e->msg.empty() ? std::string("packed batch executor stopped") : e->msg;
+}
 
 }  // namespace eik

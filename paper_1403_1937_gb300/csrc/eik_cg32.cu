@@ -771,9 +771,11 @@ k_cg2d_batch(const __grid_constant__ CUtensorMap tm_r0, const __grid_constant__ 
   extern __shared__ __align__(128) unsigned char cgb_raw[];
   __shared__ __align__(8) uint64_t bars[WPB * NS];
   __shared__ int ktabs[WPB * kTab];
+  // a pass that timed out abandons the solve: the passes left in the graph
+  // return at once (the next solve resets the list and the flag)
+  if (bc->fault) return;
   const int m = bc->m;
   const int ntot = bc->ntiles;
-  const long long nodes0 = bc->nodes;
   float *cgb_smem = reinterpret_cast<float *>(
       (reinterpret_cast<uintptr_t>(cgb_raw) + 127) & ~uintptr_t(127));
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -788,11 +790,13 @@ k_cg2d_batch(const __grid_constant__ CUtensorMap tm_r0, const __grid_constant__ 
   // lane 0: the next row to copy (tile, step, atlas row of the tile's y0,
   // the buffer set its instance reads)
   int nx_q = 0, nx_j = 0, nx_x0 = 0, nx_row = 0, nx_dir = 1, nx_t = gw, nx_rs = 0;
+  int withhold = 0;   // test hook (MixCtl.withhold): warp 0 never gets its first row
   auto set_tile = [&](int t) {
     nx_t = t;
     if (t >= ntot) return;
     const int a = batch_find(pre, m, t);
     const int inst = act[a];
+    if (nx_q == 0 && gw == 0 && st[inst].withhold && st[inst].first) withhold = 1;
     const int local = t - pre[a];
     const int tx = bi[inst].tiles_x;
     const int cyk = local / tx;
@@ -805,10 +809,12 @@ k_cg2d_batch(const __grid_constant__ CUtensorMap tm_r0, const __grid_constant__ 
     const int y = (nx_dir > 0) ? nx_row - 2 + nx_j : nx_row + TY + 1 - nx_j;
     float *dst = sb + (nx_q % NS) * STAGE;
     uint64_t *b = bar + (nx_q % NS);
-    mbar_expect_tx(b, 3u * kWin * 4u);
-    tma_load_2d(dst + OR, nx_rs ? &tm_r1 : &tm_r0, nx_x0 - 4, y, b);
-    tma_load_2d(dst + OP, nx_rs ? &tm_p1 : &tm_p0, nx_x0 - 4, y, b);
-    tma_load_2d(dst + OS, &tm_s, nx_x0 - 4, y, b);
+    if (!(nx_q == 0 && withhold)) {
+      mbar_expect_tx(b, 3u * kWin * 4u);
+      tma_load_2d(dst + OR, nx_rs ? &tm_r1 : &tm_r0, nx_x0 - 4, y, b);
+      tma_load_2d(dst + OP, nx_rs ? &tm_p1 : &tm_p0, nx_x0 - 4, y, b);
+      tma_load_2d(dst + OS, &tm_s, nx_x0 - 4, y, b);
+    }
     ++nx_q;
     if (++nx_j == steps) {
       nx_j = 0;
@@ -854,7 +860,7 @@ k_cg2d_batch(const __grid_constant__ CUtensorMap tm_r0, const __grid_constant__ 
     g.boundary = B.boundary;
     const CellGrid cg = B.cg;
     const int *__restrict__ kx = B.kx;
-    const int64_t rowoff = (int64_t)B.row0 * P;
+    const int row0 = B.row0;
     const int cyk = local / B.tiles_x;
     const int x0 = (local - cyk * B.tiles_x) * kW;
     const int y0 = cyk * TY;
@@ -902,7 +908,7 @@ k_cg2d_batch(const __grid_constant__ CUtensorMap tm_r0, const __grid_constant__ 
       }
       const int y = ystart + dir * j;
       if (j >= 2 && j < TY + 2 && y < g.ny && st_ok) {
-        const int64_t o = rowoff + (int64_t)y * P + xl;
+        const int64_t o = (int64_t)(row0 + y) * P + xl;
         dq0 = ld4(d + o);
         if (check) xq0 = __ldg(reinterpret_cast<const float4 *>(xref + o));
       }
@@ -1004,7 +1010,7 @@ k_cg2d_batch(const __grid_constant__ CUtensorMap tm_r0, const __grid_constant__ 
             if (check && fabsf(rv[i]) > thetaF * fabsf(xv[i] + dn[i])) bad = 1;
           }
           if (st_ok) {
-            const int64_t o = rowoff + (int64_t)y2 * P + xl;
+            const int64_t o = (int64_t)(row0 + y2) * P + xl;
             st4(d + o, dn[0], dn[1], dn[2], dn[3]);
             st4((wset ? r1 : r0) + o, rv[0] * gwr, rv[1] * gwr, rv[2] * gwr, rv[3] * gwr);
             st4((wset ? p1 : p0) + o, pv[0] * gwr, pv[1] * gwr, pv[2] * gwr, pv[3] * gwr);
@@ -1022,11 +1028,19 @@ k_cg2d_batch(const __grid_constant__ CUtensorMap tm_r0, const __grid_constant__ 
       }
     }
     if (fault) break;
-    batch_tile_done(gam, dlt, rmax, pmax, bad, pap, t, inst, a, pre, st, cnt, alive, bc, part,
-                    part_cap, done);
+    {
+      // the tile's list entry again (not kept live through the tile)
+      const int te = gw + k * nw;
+      const int ae = batch_find(pre, m, te);
+      batch_tile_done(gam, dlt, rmax, pmax, bad, pap, te, act[ae], ae, pre, st, cnt, alive, bc,
+                      part, part_cap, done);
+    }
   }
   if (fault && l0) {
-    for (int qq = q; qq < nx_q; ++qq) mbar_wait_bounded(&bar[qq % NS], (uint32_t)(qq / NS) & 1u);
+    // leave no copy in flight: wait (bounded) for every row issued and not
+    // yet waited for
+    for (int qq = q; qq < nx_q; ++qq)
+      if (!(qq == 0 && withhold)) mbar_wait_bounded(&bar[qq % NS], (uint32_t)(qq / NS) & 1u);
     atomicExch(&bc->fault, 1);
   }
   __syncwarp();
@@ -1039,6 +1053,7 @@ k_cg2d_batch(const __grid_constant__ CUtensorMap tm_r0, const __grid_constant__ 
   lastw = __shfl_sync(0xffffffffu, lastw, 0);
   if (!lastw) return;
   __threadfence();
+  const long long nodes0 = __ldcg(&bc->nodes);   // this pass's (the update rewrites it)
   batch_list_update(bi, st, act, pre, cnt, alive, bc, ring, ring_cap, m, TY, set ^ 1);
   if (l0) {
     bc->warps_done = 0u;

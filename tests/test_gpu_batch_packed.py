@@ -163,3 +163,23 @@ def test_packed_repeated_solves_and_new_f(eik):
     for inst, Si in zip(insts, b.split(S3.cpu().numpy())):
         assert np.max(np.abs(Si.ravel() - oracle_S(inst))) <= S_ABS
     eik.eik_destroy_batch(b)
+
+
+def test_packed_timeout_path(eik):
+    """Test hook (eik_options.test_flags bit 0): in the first pass one warp
+    never gets its first row copy, its bounded wait (0.2 s) expires, the pass
+    flags the fault, the executor abandons the solve and every instance
+    returns EIK_ERR_TIMEOUT; no GPU fault is involved.  A batch created
+    without the hook then solves normally."""
+    from paper_1403_1937_gb300 import _lib
+    insts = ragged(4, 31, side=(40, 160))
+    opt = eik.make_options(precision="mixed", tol=1e-7, tile_override=1, batch_tile_rows=16,
+                           test_flags=1)
+    b = eik.eik_create_batch(insts, opt)
+    with pytest.raises(_lib.EikError) as ei:
+        eik.eik_solve_batch(b)
+    assert ei.value.status == _lib.EIK_ERR_TIMEOUT
+    eik.eik_destroy_batch(b)
+    parts, _, _ = solve_packed(eik, insts, tile_override=1, batch_tile_rows=16)
+    for inst, Si in zip(insts, parts):
+        assert np.max(np.abs(Si - oracle_S(inst))) <= S_ABS
