@@ -418,7 +418,7 @@ def secondary_block(args, ws, local):
     return out
 
 
-def run_diff(args):
+def run_diff(args, emit=True):
     """Differentiation workload (config 5): 32 instances of 512^2, one source
     each; a step is the forward solve of the batch, dL/dS = 2 (S - T) on 4096
     receivers per instance, and the adjoint solve giving dL/df.  The targets
@@ -502,10 +502,13 @@ def run_diff(args):
             "iterations_per_step": {"forward": fwd_it / args.steps,
                                     "adjoint": adj_it / args.steps},
             "loss": loss}
-    print(json.dumps(line), flush=True)
+    eik.eik_destroy_batch(b)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
-def run_batch(args):
+def run_batch(args, emit=True):
     """Batched workload: independent 2D instances of uneven size, f, sources
     and hbar (config 4), solved together through eik_solve_batch."""
     import torch
@@ -591,8 +594,9 @@ def run_batch(args):
             "batch": {k: info1[k] for k in ("packed", "variant", "tile_rows", "tuned")},
             "roofline": roof}
     eik.eik_destroy_batch(b)
-    if rank == 0:
+    if emit:
         print(json.dumps(line), flush=True)
+    return line
 
 
 def fft_flops(n, terms):
@@ -741,6 +745,29 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def other_blocks(args):
+    """The batched workload (packed, autotuned; 1 warm-up + 2 timed solves)
+    and the differentiation workload (1 + 1 steps), each as a compact summary
+    of its own bench line, for the default single-GPU run."""
+    import copy
+    out = {}
+    a4 = copy.copy(args)
+    a4.workload, a4.tol, a4.steps, a4.warmup = "c4", 1e-7, 2, 1
+    a4.tile_override, a4.batch_pack, a4.batch_tile_rows = 0, 0, 0
+    l4 = run_batch(a4, emit=False)
+    out["c4"] = {k: l4[k] for k in ("value", "unit", "ms_per_step", "steps", "warmup", "iterations",
+                                    "batch", "roofline", "clocks")}
+    out["c4"]["workload"] = l4["config"]["workload"]
+    a5 = copy.copy(args)
+    a5.workload, a5.tol, a5.steps, a5.warmup = "c5", 1e-6, 1, 1
+    a5.tile_override, a5.batch_pack, a5.batch_tile_rows = 0, 0, 0
+    l5 = run_diff(a5, emit=False)
+    out["c5"] = {k: l5[k] for k in ("value", "unit", "ms_per_step", "steps", "warmup",
+                                    "iterations_per_step", "dtype", "clocks")}
+    out["c5"]["workload"] = l5["config"]["workload"]
+    return out
+
+
 def main():
     args = parse()
     if args.tol is None:
@@ -761,6 +788,10 @@ def main():
     c3 = None
     if args.workload == "c2" and not args.no_c3_block:
         c3 = secondary_block(args, ws, int(os.environ.get("LOCAL_RANK", "0")))
+    batch_blocks = {}
+    if args.workload == "c2" and not args.no_c3_block and ws == 1:
+        # the batched and differentiation workloads, briefly, in the same run
+        batch_blocks = other_blocks(args)
     if rank != 0:
         return
     head = results.get(args.precision, {})
@@ -802,6 +833,7 @@ def main():
     }
     if c3 is not None:
         line["c3"] = c3
+    line.update(batch_blocks)
     print(json.dumps(line), flush=True)
 
 
