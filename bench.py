@@ -602,12 +602,18 @@ def run_batch(args, emit=True):
 def fft_flops(n, terms):
     """FP64 operations of the 1D transforms eik_fft_series runs on an n x n
     grid with `terms` terms, at the usual 5 N log2 N per complex transform of
-    length N: transform length P = the power of two >= 2n - 1; the kernels'
-    transforms (G~, and G when terms > 0) take 2P row transforms, a grid
-    function's forward transform n + P and its inverse P + n."""
-    P = 1
-    while P < 2 * n - 1:
-        P *= 2
+    length N: transform length P = the smallest 2^a 3^b 5^c >= 2n - 1; the
+    kernels' transforms (G~, and G when terms > 0) take 2P row transforms, a
+    grid function's forward transform n + P and its inverse P + n."""
+    P = max(2 * n - 1, 2)
+    while True:
+        q = P
+        for fct in (2, 3, 5):
+            while q % fct == 0:
+                q //= fct
+        if q == 1:
+            break
+        P += 1
     per = 5 * P * np.log2(P)
     kernels = 2 * P * (1 + (1 if terms > 0 else 0))
     data = (1 + terms) * 2 * (n + P)

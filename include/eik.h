@@ -346,10 +346,10 @@ eik_status eik_sfs_forcing(const double *P, int64_t n, double f_min, double *f,
  * (Eqs. phiRecRelation, phi_i_Solution; G = K_0(f~|x|/hbar)/(2 pi hbar^2),
  * Eq. GreensFunction2D, averaged over the grid cell at the origin); then
  * S = -hbar log phi (Eq. SfromPhi).  Convolutions are linear over the grid,
- * by FP64 transforms of arrays zero-padded to the next power of two
- * >= 2n - 1 per axis.  This is the paper's first solver, kept as a second
- * workload: the finite-difference solve above is the main path.
- *   dims        (nx, ny), each 2 .. 4096; node (x, y) is f[x + nx y].
+ * by FP64 mixed-radix transforms of arrays zero-padded to the smallest
+ * 2^a 3^b 5^c >= 2n - 1 per axis.  This is the paper's first solver, kept as
+ * a second workload: the finite-difference solve above is the main path.
+ *   dims        (nx, ny), each 2 .. 3600; node (x, y) is f[x + nx y].
  *   h, hbar     > 0.
  *   f           nx ny values, > 0 (host or device).
  *   src_idx     nsrc >= 1 flat node indices (host or device).

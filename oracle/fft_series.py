@@ -23,9 +23,10 @@ Readings (where the paper is silent):
 
 * F1: a discrete convolution of two grid functions is the linear (aperiodic)
   one over the grid, sum_j K(x_i - x_j) g_j; the transforms are of arrays
-  zero-padded to P_a >= 2 n_a - 1 points per axis (the next power of two),
-  with the kernel sampled at the offsets -(n_a - 1) .. n_a - 1 and wrapped,
-  so that no product wraps onto the grid.
+  zero-padded to P_a >= 2 n_a - 1 points per axis (here the next power of
+  two; any P_a >= 2 n_a - 1 gives the same convolution up to rounding), with
+  the kernel sampled at the offsets -(n_a - 1) .. n_a - 1 and wrapped, so that
+  no product wraps onto the grid.
 * F2: G is singular at the origin; its sample at offset 0 is the average of
   G over the grid cell [-h/2, h/2]^2, using int_0^R r K_0(a r) dr =
   (1 - a R K_1(a R)) / a^2 along each ray of the cell.

@@ -138,7 +138,7 @@ def test_fft_series_validates_arguments_without_gpu(lib):
     P = ctypes.c_void_p(0x1000)      # never dereferenced: the checks fail first
     d = (ctypes.c_int64 * 2)(9, 7)
     ft = ctypes.c_double()
-    for dims in ((1, 7), (9, 1), (4097, 8), (8, 4097)):
+    for dims in ((1, 7), (9, 1), (3601, 8), (8, 3601)):
         dd = (ctypes.c_int64 * 2)(*dims)
         assert lib.eik_fft_series(dd, 0.1, 0.1, P, P, 1, 2, 0.0, P, None, ctypes.byref(ft),
                                   None) == _lib.EIK_ERR_ARG, dims
