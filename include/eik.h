@@ -72,6 +72,18 @@ enum {
 };
 
 enum {
+  EIK_PRECOND_JACOBI = 0,     /* Jacobi-PCG, one fused pass per iteration */
+  EIK_PRECOND_MULTIGRID = 1   /* 2D: PCG with a V-cycle of relative-form
+                                 aggregation multigrid (Sec. 6 names
+                                 multigrid as the O(N) route for the sparse
+                                 system): coarse basis functions are the
+                                 estimated phi = exp(-S/hbar) on 2 x 2
+                                 boxes, so coarse corrections are relative
+                                 ones and the far field converges with the
+                                 near field */
+};
+
+enum {
   EIK_STOP_COMPONENTWISE = 0, /* max_i |r_i| / (a_ii phi_i) <= tol */
   EIK_STOP_NORMWISE = 1       /* ||r_hat||_2 / ||b_hat||_2 <= tol (Jacobi-scaled) */
 };
@@ -126,7 +138,15 @@ typedef struct {
   int batch_tile_rows;/* packed batches: rows per tile of the packed pass
                          (1..1024); 0 = autotuned.  tile_override (1..4)
                          fixes the pass's 2D variant; 0 = autotuned. */
-  int reserved[3];
+  int precond;        /* EIK_PRECOND_*: preconditioner of the FP32 inner
+                         solve in mixed mode; default EIK_PRECOND_JACOBI.
+                         EIK_PRECOND_MULTIGRID needs EIK_PREC_MIXED and a 2D
+                         grid (else EIK_ERR_ARG); its solves sweep level-set
+                         bands only when phi spans more than 256 powers of
+                         two (bands of 128; band_bits overrides both as for
+                         Jacobi), and a batch of such instances solves per
+                         instance (batch_pack is ignored). */
+  int reserved[2];
 } eik_options;
 
 typedef struct {

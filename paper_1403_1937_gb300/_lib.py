@@ -30,6 +30,8 @@ PREC_FP64 = 0
 PREC_MIXED = 1
 STOP_COMPONENTWISE = 0
 STOP_NORMWISE = 1
+PRECOND_JACOBI = 0
+PRECOND_MULTIGRID = 1
 BOUNDARY_HALF_CELL = 0
 BOUNDARY_DROP_EDGE = 1
 
@@ -41,7 +43,7 @@ class Options(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
                 ("band_bits", ctypes.c_int), ("test_flags", ctypes.c_int),
                 ("batch_pack", ctypes.c_int), ("batch_tile_rows", ctypes.c_int),
-                ("reserved", ctypes.c_int * 3)]
+                ("precond", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 class Stats(ctypes.Structure):

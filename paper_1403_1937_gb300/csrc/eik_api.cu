@@ -432,6 +432,10 @@ static eik_status create_impl(eik_handle **out, int ndim, const int64_t *dims, d
     return fail(EIK_ERR_ARG, "batch_pack must be -1, 0 or 1");
   if (o.batch_tile_rows < 0 || o.batch_tile_rows > 1024)
     return fail(EIK_ERR_ARG, "batch_tile_rows must be in 0..1024");
+  if (o.precond != EIK_PRECOND_JACOBI && o.precond != EIK_PRECOND_MULTIGRID)
+    return fail(EIK_ERR_ARG, "unknown precond");
+  if (o.precond == EIK_PRECOND_MULTIGRID && (o.precision != EIK_PREC_MIXED || ndim != 2))
+    return fail(EIK_ERR_ARG, "the multigrid preconditioner needs mixed precision and a 2D grid");
 
   eik_handle *h = new (std::nothrow) eik_handle();
   if (!h) return fail(EIK_ERR_OOM, "host allocation failed");
@@ -538,7 +542,7 @@ static eik_status create_impl(eik_handle **out, int ndim, const int64_t *dims, d
       eik_status ms = exec ? mixed_create_member(&h->mixed, g, h->tc, h->num_sms, exec, member,
                                                  h->stream)
                            : mixed_create(&h->mixed, g, h->tc, h->num_sms, o.tile_override,
-                                          h->stream);
+                                          o.precond, h->stream);
       if (ms != EIK_OK) {
         free_handle(h);
         return fail(ms, "mixed-precision workspace allocation failed");
@@ -850,7 +854,8 @@ eik_status eik_create_batch(eik_batch **out, int count, int ndim, const int64_t 
   eik_options o;
   eik_default_options(&o);
   if (opt) o = *opt;
-  if (ndim == 2 && o.precision == EIK_PREC_MIXED && o.batch_pack >= 0) {
+  if (ndim == 2 && o.precision == EIK_PREC_MIXED && o.batch_pack >= 0 &&
+      o.precond == EIK_PRECOND_JACOBI) {
     // packed: one atlas for the FP32 arrays of every instance
     std::vector<int> nx(count), ny(count);
     for (int i = 0; i < count; ++i) {

@@ -1,0 +1,681 @@
+// Multigrid-preconditioned inner solve of the mixed-precision path (2D).
+//
+// The paper names multigrid as the O(N) route for the sparse system of
+// Sec. 6 (Eq. sparse-system); this file builds one that keeps the relative
+// accuracy the method needs.  phi = exp(-S/hbar) spans hundreds of powers of
+// two, and a componentwise tolerance asks for the far field as precisely as
+// the near field, so the coarse spaces are built in relative form:
+//
+// * Level 0 is the Jacobi-scaled operator of the correction equation in kx
+//   units, (A v)_i = v_i - sig_i sum_j omega_ij sig_j 2^(kx_i - kx_j) v_j,
+//   exactly as in the Jacobi-preconditioned inner CG.
+// * Coarse node C of level l + 1 aggregates a 2 x 2 box of level-l nodes.
+//   Its basis function is, on level 0, the estimated solution shape
+//   w_i = exp(kx_i ln 2 - St_i / hbar) / sig_i on the box (St_i: the cell
+//   distance estimate interpolated bilinearly between cell centres), so a
+//   coarse unknown is a relative correction, constant on its box, of the
+//   estimated phi.  Coarser levels take unit weights, so every coarse basis
+//   function keeps that level-0 shape.
+// * Every level l holds its Galerkin operator A^l = P^T A^(l-1) P (true,
+//   symmetric) for vectors stored as value * 2^k, k a power-of-two exponent
+//   per node: (A y)_C = a_C y_C + sum_D c_CD y_D with the row-relative
+//   coefficients c_CD = A_CD 2^(k_C - k_D), one per neighbour (west, east,
+//   south, north), formed in FP64.  Between an aggregate and its upstream
+//   neighbour (nearer the sources) c is O(1); downstream it is tiny or 0.
+//   (Storing A_CD and the factor separately would overflow FP32 on coarse
+//   levels, where neighbouring exponents differ by over a hundred.)  The
+//   transfers in these units: restriction g_C = sum_{i in C} P_i 2^(k_C -
+//   k_i) t_i, prolongation y_i += P_i 2^(k_i - k_C) y_C, with P_i = w_i on
+//   level 0 (one exponent per box there) and P_i = 2^(k_C - k_i), k_C = min
+//   over the box, above; so c^(l+1)_CD = sum_{i in C, j in D} 2^(2(k_C -
+//   k_i)) c_ij and a^(l+1)_C = sum_{i in C} 2^(2(k_C - k_i)) (a_i + sum_{j in
+//   C} c_ij).
+// * The cycle is a symmetric V-cycle down to one node: one damped-Jacobi
+//   sweep (omega = 8/9) before and after each coarse correction, the single
+//   node solved exactly.  Sources (sig = 0) take no part in any transfer.
+//
+// The outer iteration is preconditioned CG on level 0 in kx units with the
+// true inner product, <u, v> = sum u_i v_i 2^(-2 kx_i) (FP64 sums, weights
+// relative to the smallest exponent; a weight below the FP64 range is 0),
+// one graph launch per two iterations:
+//   z = M r, rho = <r, z>, beta = rho / rho_old, p = z + beta p, q = A p,
+//   alpha = rho / <p, q>, d += alpha p, r -= alpha q,
+// and the inner solve stops on the mixed solve's tests (scaled max norm of r
+// or the componentwise test against the iterate).  Measured on a CPU model of
+// this scheme (FP32 inner vectors, FP64 refinement): 56 inner iterations
+// instead of 998 for Jacobi-PCG on a 513^2 workload with hbar = 10.2 h, and
+// 72 / 79 with hbar = 4 h / 2 h (phi down to e^-128, no level-set bands).
+#include <cuda.h>
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <climits>
+#include <string>
+#include <vector>
+
+#include "eik_mg.h"
+
+namespace eik {
+
+namespace {
+
+constexpr float kOmega = 8.0f / 9.0f;   // Chebyshev-optimal single step on [1/4, 2]
+constexpr int kGraphIters = 2;          // even: the direction buffers alternate
+// an inner solve that has not met its test after this many iterations ends
+// (the refinement step then judges progress from the true residual)
+constexpr int kMaxInnerIters = 1000;
+thread_local std::string g_msg = "no error";
+
+struct MgLevel {
+  int nx = 0, ny = 0;
+  float *a = nullptr;            // diagonal; a < 0 marks a node with no unknowns
+  float *c = nullptr;            // 4 x nx*ny row-relative coefficients: W, E, S, N
+  int *k = nullptr;
+  float *g = nullptr, *y = nullptr;
+};
+enum { kW = 0, kE = 1, kS = 2, kN = 3 };
+
+struct MgCtl {
+  double rho;        // <r, z> of the current residual
+  double alpha, beta;
+  int iter, max_iter, done, status, stalled, mode, first, kmin;
+  float thresh, theta;
+  unsigned int counter[4];
+};
+
+__device__ __forceinline__ int kx_at(const CellGrid &cg, int x, int y, const int *kx) {
+  return kx[(x >> cg.lgB) + cg.cx * (y >> cg.lgB)];
+}
+__device__ __forceinline__ float face(int i, int n, int boundary) {
+  return (boundary == EIK_BOUNDARY_HALF_CELL && (i == 0 || i == n - 1)) ? 0.5f : 1.f;
+}
+__device__ __forceinline__ float p2f(int e) { return ldexpf(1.f, e); }
+
+// Level-0 off-diagonal sum  sig_i sum_j omega_ij sig_j 2^(k_i - k_j) v(j)
+// for the node (x, y), v given by a functor of the pitched index.
+template <class V>
+__device__ __forceinline__ float nb0(const Grid &g, const CellGrid &cg, int px,
+                                     const float *__restrict__ s32, const int *__restrict__ kx,
+                                     int x, int y, int ki, V v) {
+  float acc = 0.f;
+  const float hy = face(y, g.ny, g.boundary), hx = face(x, g.nx, g.boundary);
+  const int64_t i = (int64_t)y * px + x;
+  if (x > 0) acc += hy * s32[i - 1] * p2f(ki - kx_at(cg, x - 1, y, kx)) * v(i - 1);
+  if (x + 1 < g.nx) acc += hy * s32[i + 1] * p2f(ki - kx_at(cg, x + 1, y, kx)) * v(i + 1);
+  if (y > 0) acc += hx * s32[i - px] * p2f(ki - kx_at(cg, x, y - 1, kx)) * v(i - px);
+  if (y + 1 < g.ny) acc += hx * s32[i + px] * p2f(ki - kx_at(cg, x, y + 1, kx)) * v(i + px);
+  return s32[i] * acc;
+}
+
+// Coarse-level operator (A u)_C for node (x, y) of a level, u by functor of
+// the dense index.
+template <class V>
+__device__ __forceinline__ float apply_l(const MgLevel &L, int x, int y, V u) {
+  const int64_t i = (int64_t)y * L.nx + x;
+  const int64_t m = (int64_t)L.nx * L.ny;
+  float acc = fabsf(L.a[i]) * u(i);
+  if (x > 0) acc = fmaf(L.c[kW * m + i], u(i - 1), acc);
+  if (x + 1 < L.nx) acc = fmaf(L.c[kE * m + i], u(i + 1), acc);
+  if (y > 0) acc = fmaf(L.c[kS * m + i], u(i - L.nx), acc);
+  if (y + 1 < L.ny) acc = fmaf(L.c[kN * m + i], u(i + L.nx), acc);
+  return acc;
+}
+
+// ------------------------------------------------------------- setup
+// w_i = exp(kx_i ln 2 - St_i / hbar) / sig_i (0 on the sources); St_i
+// bilinear between the cell centres (flat beyond the outer ones).
+__global__ void k_mg_weights(Grid g, CellGrid cg, int px, const float *__restrict__ s32,
+                             const int *__restrict__ kx, const float *__restrict__ St,
+                             float *__restrict__ w) {
+  const int64_t n = (int64_t)g.nx * g.ny;
+  const float B = (float)cg.B, half = 0.5f * (B - 1.f);
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(t % g.nx), y = (int)(t / g.nx);
+    const int64_t i = (int64_t)y * px + x;
+    const float s = s32[i];
+    if (s == 0.f) {
+      w[i] = 0.f;
+      continue;
+    }
+    auto axis = [&](int c, int ncell, int nn, int &I0, int &I1, float &tt) {
+      I0 = min(max((int)floorf(((float)c - half) / B), 0), ncell - 1);
+      I1 = min(I0 + 1, ncell - 1);
+      const float c0 = fminf(I0 * B + half, (float)(nn - 1));
+      const float c1 = fminf(I1 * B + half, (float)(nn - 1));
+      tt = (c1 > c0) ? fminf(fmaxf(((float)c - c0) / (c1 - c0), 0.f), 1.f) : 0.f;
+    };
+    int I0, I1, J0, J1;
+    float tx, ty;
+    axis(x, cg.cx, g.nx, I0, I1, tx);
+    axis(y, cg.cy, g.ny, J0, J1, ty);
+    const float s00 = St[I0 + cg.cx * J0], s10 = St[I1 + cg.cx * J0];
+    const float s01 = St[I0 + cg.cx * J1], s11 = St[I1 + cg.cx * J1];
+    const int ki = kx_at(cg, x, y, kx);
+    float ex = 0.f;
+    if (isfinite(s00) && isfinite(s10) && isfinite(s01) && isfinite(s11)) {
+      const float Sb = (1.f - ty) * ((1.f - tx) * s00 + tx * s10) + ty * ((1.f - tx) * s01 + tx * s11);
+      ex = (float)((double)ki * 0.69314718055994530942 - (double)Sb / g.hbar);
+      ex = fminf(fmaxf(ex, -30.f), 30.f);   // w^2 stays in the FP32 range
+    }
+    w[i] = expf(ex) / s;
+  }
+}
+
+// Level 1 from level 0: P_i = w_i (one exponent per 2 x 2 box: boxes lie
+// inside one cell), true A_ij = -sig_i sig_j omega_ij; c_CD = 2^(k_C - k_D)
+// sum w_i w_j A_ij over the edges between the two boxes.  Sums in FP64.
+__global__ void k_mg_coarsen0(Grid g, CellGrid cg, int px, const float *__restrict__ s32,
+                              const int *__restrict__ kx, const float *__restrict__ w, MgLevel L) {
+  const int64_t m = (int64_t)L.nx * L.ny;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int X = (int)(t % L.nx), Y = (int)(t / L.nx);
+    const int x0 = 2 * X, y0 = 2 * Y;
+    const int x1 = min(x0 + 1, g.nx - 1), y1 = min(y0 + 1, g.ny - 1);
+    auto W = [&](int x, int y) { return (double)w[(int64_t)y * px + x]; };
+    auto S = [&](int x, int y) { return (double)s32[(int64_t)y * px + x]; };
+    // A_ij of the x-edge (xa, y)-(xa + 1, y) and of the y-edge (x, ya)-(x, ya + 1)
+    auto ax = [&](int xa, int y) {
+      return -S(xa, y) * S(xa + 1, y) * (double)face(y, g.ny, g.boundary);
+    };
+    auto ay = [&](int x, int ya) {
+      return -S(x, ya) * S(x, ya + 1) * (double)face(x, g.nx, g.boundary);
+    };
+    const int kc = kx_at(cg, x0, y0, kx);
+    double A = 0.0, cW = 0.0, cE = 0.0, cS = 0.0, cN = 0.0;
+    bool live = false;
+    for (int y = y0; y <= y1; ++y)
+      for (int x = x0; x <= x1; ++x) {
+        const double wi = W(x, y);
+        if (wi != 0.0) live = true;
+        A += wi * wi;
+      }
+    if (x1 > x0)
+      for (int y = y0; y <= y1; ++y) A += 2.0 * W(x0, y) * W(x1, y) * ax(x0, y);
+    if (y1 > y0)
+      for (int x = x0; x <= x1; ++x) A += 2.0 * W(x, y0) * W(x, y1) * ay(x, y0);
+    if (X > 0) {
+      const double f = ldexp(1.0, kc - kx_at(cg, x0 - 2, y0, kx));
+      for (int y = y0; y <= y1; ++y) cW += W(x0, y) * W(x0 - 1, y) * ax(x0 - 1, y);
+      cW *= f;
+    }
+    if (X + 1 < L.nx && x0 + 2 < g.nx) {
+      const double f = ldexp(1.0, kc - kx_at(cg, x0 + 2, y0, kx));
+      for (int y = y0; y <= y1; ++y) cE += W(x1, y) * W(x0 + 2, y) * ax(x1, y);
+      cE *= f;
+    }
+    if (Y > 0) {
+      const double f = ldexp(1.0, kc - kx_at(cg, x0, y0 - 2, kx));
+      for (int x = x0; x <= x1; ++x) cS += W(x, y0) * W(x, y0 - 1) * ay(x, y0 - 1);
+      cS *= f;
+    }
+    if (Y + 1 < L.ny && y0 + 2 < g.ny) {
+      const double f = ldexp(1.0, kc - kx_at(cg, x0, y0 + 2, kx));
+      for (int x = x0; x <= x1; ++x) cN += W(x, y1) * W(x, y0 + 2) * ay(x, y1);
+      cN *= f;
+    }
+    L.a[t] = live ? (float)A : -1.f;
+    L.c[kW * m + t] = live ? (float)cW : 0.f;
+    L.c[kE * m + t] = live ? (float)cE : 0.f;
+    L.c[kS * m + t] = live ? (float)cS : 0.f;
+    L.c[kN * m + t] = live ? (float)cN : 0.f;
+    L.k[t] = kc;
+  }
+}
+
+// Smallest exponent over the live nodes of the box (X, Y) of level F;
+// INT_MAX when it has none.
+__device__ __forceinline__ int box_k(const MgLevel &F, int X, int Y) {
+  int k = INT_MAX;
+  for (int y = 2 * Y; y <= min(2 * Y + 1, F.ny - 1); ++y)
+    for (int x = 2 * X; x <= min(2 * X + 1, F.nx - 1); ++x) {
+      const int64_t i = (int64_t)y * F.nx + x;
+      if (F.a[i] >= 0.f) k = min(k, F.k[i]);
+    }
+  return k;
+}
+
+// Level l + 1 (C) from level l (F): rows restricted with 2^(2(k_C - k_i)),
+// columns prolonged with unit weight (live nodes only).
+__global__ void k_mg_coarsen(MgLevel F, MgLevel C) {
+  const int64_t m = (int64_t)C.nx * C.ny;
+  const int64_t mf = (int64_t)F.nx * F.ny;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int X = (int)(t % C.nx), Y = (int)(t / C.nx);
+    const int kc = box_k(F, X, Y);
+    if (kc == INT_MAX) {
+      C.a[t] = -1.f;
+      for (int d = 0; d < 4; ++d) C.c[d * m + t] = 0.f;
+      C.k[t] = F.k[(int64_t)(2 * Y) * F.nx + 2 * X];
+      continue;
+    }
+    const int x0 = 2 * X, y0 = 2 * Y;
+    const int x1 = min(x0 + 1, F.nx - 1), y1 = min(y0 + 1, F.ny - 1);
+    double A = 0.0, cW = 0.0, cE = 0.0, cS = 0.0, cN = 0.0;
+    for (int y = y0; y <= y1; ++y)
+      for (int x = x0; x <= x1; ++x) {
+        const int64_t i = (int64_t)y * F.nx + x;
+        if (F.a[i] < 0.f) continue;
+        const double r = ldexp(1.0, 2 * (kc - F.k[i]));
+        double row = (double)F.a[i];
+        // neighbours inside the box join the diagonal, the others the links
+        if (x > 0) (x - 1 >= x0 ? row : cW) += (x - 1 >= x0 ? 1.0 : r) * (double)F.c[kW * mf + i];
+        if (x + 1 < F.nx) (x + 1 <= x1 ? row : cE) += (x + 1 <= x1 ? 1.0 : r) * (double)F.c[kE * mf + i];
+        if (y > 0) (y - 1 >= y0 ? row : cS) += (y - 1 >= y0 ? 1.0 : r) * (double)F.c[kS * mf + i];
+        if (y + 1 < F.ny) (y + 1 <= y1 ? row : cN) += (y + 1 <= y1 ? 1.0 : r) * (double)F.c[kN * mf + i];
+        A += r * row;
+      }
+    C.a[t] = (float)A;
+    C.c[kW * m + t] = (X > 0) ? (float)cW : 0.f;
+    C.c[kE * m + t] = (X + 1 < C.nx) ? (float)cE : 0.f;
+    C.c[kS * m + t] = (Y > 0) ? (float)cS : 0.f;
+    C.c[kN * m + t] = (Y + 1 < C.ny) ? (float)cN : 0.f;
+    C.k[t] = kc;
+  }
+}
+
+// ------------------------------------------------------------- V-cycle
+// Level 0 down: y = omega r, t = r - A y, g1 = sum over the box of w_i t_i.
+__global__ void k_mg_down0(Grid g, CellGrid cg, int px, const float *__restrict__ s32,
+                           const int *__restrict__ kx, const float *__restrict__ w,
+                           const float *__restrict__ r, MgLevel L1, const MgCtl *ctl) {
+  if (ctl->done) return;
+  const int64_t n = (int64_t)L1.nx * L1.ny;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int X = (int)(t % L1.nx), Y = (int)(t / L1.nx);
+    float sum = 0.f;
+    for (int y = 2 * Y; y <= min(2 * Y + 1, g.ny - 1); ++y)
+      for (int x = 2 * X; x <= min(2 * X + 1, g.nx - 1); ++x) {
+        const int64_t i = (int64_t)y * px + x;
+        const float wi = w[i];
+        if (wi == 0.f) continue;
+        const int ki = kx_at(cg, x, y, kx);
+        const float off = nb0(g, cg, px, s32, kx, x, y, ki, [&](int64_t j) { return r[j]; });
+        // (A (omega r))_i = omega (r_i - off)
+        const float ti = r[i] - kOmega * (r[i] - off);
+        sum = fmaf(wi, ti, sum);
+      }
+    L1.g[t] = sum;
+  }
+}
+
+// Level l down (l >= 1): y = omega g / a, t = g - A y, restricted to l + 1.
+__global__ void k_mg_down(MgLevel F, MgLevel C, const MgCtl *ctl) {
+  if (ctl->done) return;
+  const int64_t n = (int64_t)C.nx * C.ny;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int X = (int)(t % C.nx), Y = (int)(t / C.nx);
+    const int kc = C.k[t];
+    float sum = 0.f;
+    if (C.a[t] >= 0.f) {
+      auto yv = [&](int64_t j) { return kOmega * F.g[j] / fabsf(F.a[j]); };
+      for (int y = 2 * Y; y <= min(2 * Y + 1, F.ny - 1); ++y)
+        for (int x = 2 * X; x <= min(2 * X + 1, F.nx - 1); ++x) {
+          const int64_t i = (int64_t)y * F.nx + x;
+          if (F.a[i] < 0.f) continue;
+          const float ti = F.g[i] - apply_l(F, x, y, yv);
+          sum = fmaf(p2f(2 * (kc - F.k[i])), ti, sum);
+        }
+    }
+    C.g[t] = sum;
+  }
+}
+
+// Coarsest level (one node per axis or a few): exact for a single node,
+// otherwise a damped-Jacobi sweep.
+__global__ void k_mg_bottom(MgLevel L, const MgCtl *ctl) {
+  if (ctl->done) return;
+  const int64_t n = (int64_t)L.nx * L.ny;
+  for (int64_t t = threadIdx.x; t < n; t += blockDim.x)
+    L.y[t] = (L.a[t] >= 0.f) ? L.g[t] / L.a[t] : 0.f;
+}
+
+// Level l up (l >= 1): u = omega g / a + y(parent); y = u + omega (g - A u) / a.
+__global__ void k_mg_up(MgLevel F, MgLevel C, const MgCtl *ctl) {
+  if (ctl->done) return;
+  const int64_t n = (int64_t)F.nx * F.ny;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(t % F.nx), y = (int)(t / F.nx);
+    if (F.a[t] < 0.f) {
+      F.y[t] = 0.f;
+      continue;
+    }
+    auto u = [&](int64_t j) {
+      const int xj = (int)(j % F.nx), yj = (int)(j / F.nx);
+      const float par = (F.a[j] >= 0.f) ? C.y[(int64_t)(yj >> 1) * C.nx + (xj >> 1)] : 0.f;
+      return kOmega * F.g[j] / fabsf(F.a[j]) + par;
+    };
+    const float ut = u(t);
+    F.y[t] = ut + kOmega * (F.g[t] - apply_l(F, x, y, u)) / F.a[t];
+  }
+}
+
+// ------------------------------------------------------------- PCG passes
+__device__ __forceinline__ double wdot(int k, int kmin) { return ldexp(1.0, 2 * (kmin - k)); }
+
+// Level 0 up: u = omega r + w y1(parent), z = u + omega (r - A u); rho = <r, z>.
+__global__ void __launch_bounds__(kThreads)
+k_mg_up0(Grid g, CellGrid cg, int px, const float *__restrict__ s32, const int *__restrict__ kx,
+         const float *__restrict__ w, const float *__restrict__ r, MgLevel L1,
+         float *__restrict__ z, MgCtl *ctl, double *part) {
+  __shared__ double sh[32];
+  __shared__ int flag;
+  if (ctl->done) return;
+  const int kmin = ctl->kmin;
+  const int64_t n = (int64_t)g.nx * g.ny;
+  double rz = 0.0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(t % g.nx), y = (int)(t / g.nx);
+    const int64_t i = (int64_t)y * px + x;
+    if (s32[i] == 0.f) {
+      z[i] = 0.f;
+      continue;
+    }
+    auto u = [&](int64_t j) {
+      const int yj = (int)(j / px), xj = (int)(j - (int64_t)yj * px);
+      return kOmega * r[j] + w[j] * L1.y[(int64_t)(yj >> 1) * L1.nx + (xj >> 1)];
+    };
+    const int ki = kx_at(cg, x, y, kx);
+    const float ui = u(i);
+    const float Au = ui - nb0(g, cg, px, s32, kx, x, y, ki, u);
+    const float zi = ui + kOmega * (r[i] - Au);
+    z[i] = zi;
+    rz += (double)r[i] * (double)zi * wdot(ki, kmin);
+  }
+  const double bs = block_sum(rz, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = bs;
+  if (!last_block(&ctl->counter[0], &flag)) return;
+  const double tot = sum_partials(part, gridDim.x, sh);
+  if (threadIdx.x == 0) {
+    ctl->beta = ctl->first ? 0.0 : tot / ctl->rho;
+    ctl->rho = tot;
+    ctl->counter[0] = 0u;
+    if (!(tot > 0.0) || !isfinite(tot)) {   // z = M r lost positivity: stop here
+      ctl->stalled = 1;
+      ctl->done = 1;
+    }
+  }
+}
+
+// p = z + beta p_old, q = A p, <p, q>; alpha = rho / <p, q>.
+__global__ void __launch_bounds__(kThreads)
+k_mg_dir(Grid g, CellGrid cg, int px, const float *__restrict__ s32, const int *__restrict__ kx,
+         const float *__restrict__ z, const float *__restrict__ p_old, float *__restrict__ p_new,
+         float *__restrict__ q, MgCtl *ctl, double *part) {
+  __shared__ double sh[32];
+  __shared__ int flag;
+  if (ctl->done) return;
+  const int kmin = ctl->kmin;
+  const float beta = (float)ctl->beta;
+  const bool first = ctl->first != 0;
+  const int64_t n = (int64_t)g.nx * g.ny;
+  double pq = 0.0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(t % g.nx), y = (int)(t / g.nx);
+    const int64_t i = (int64_t)y * px + x;
+    auto pv = [&](int64_t j) { return first ? z[j] : fmaf(beta, p_old[j], z[j]); };
+    const float pi = pv(i);
+    float qi = 0.f;
+    if (s32[i] != 0.f) {
+      const int ki = kx_at(cg, x, y, kx);
+      qi = pi - nb0(g, cg, px, s32, kx, x, y, ki, pv);
+      pq += (double)pi * (double)qi * wdot(ki, kmin);
+    }
+    p_new[i] = pi;
+    q[i] = qi;
+  }
+  const double bs = block_sum(pq, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = bs;
+  if (!last_block(&ctl->counter[1], &flag)) return;
+  const double tot = sum_partials(part, gridDim.x, sh);
+  if (threadIdx.x == 0) {
+    ctl->counter[1] = 0u;
+    ctl->first = 0;
+    if (!(tot > 0.0) || !isfinite(tot)) {
+      ctl->alpha = 0.0;
+      ctl->stalled = 1;
+      ctl->done = 1;
+    } else {
+      ctl->alpha = ctl->rho / tot;
+    }
+  }
+}
+
+// d += alpha p, r -= alpha q, and the stopping tests.
+__global__ void __launch_bounds__(kThreads)
+k_mg_step(Grid g, int px, const float *__restrict__ p, const float *__restrict__ q,
+          const float *__restrict__ xref, float *__restrict__ d, float *__restrict__ r, MgCtl *ctl,
+          double *part, int nblk_part) {
+  __shared__ double sh[32];
+  __shared__ int flag;
+  if (ctl->done) return;
+  const float alpha = (float)ctl->alpha;
+  const int mode = ctl->mode;
+  const float theta = ctl->theta;
+  const int64_t n = (int64_t)g.nx * g.ny;
+  double rmax = 0.0, viol = 0.0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(t % g.nx), y = (int)(t / g.nx);
+    const int64_t i = (int64_t)y * px + x;
+    const float di = fmaf(alpha, p[i], d[i]);
+    const float ri = fmaf(-alpha, q[i], r[i]);
+    d[i] = di;
+    r[i] = ri;
+    rmax = fmax(rmax, (double)fabsf(ri));
+    if (mode == 1 && fabsf(ri) > theta * fabsf(xref[i] + di)) viol = 1.0;
+  }
+  const double b1 = block_max(rmax, sh);
+  const double b2 = block_max(viol, sh);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = b1;
+    part[nblk_part + blockIdx.x] = b2;
+  }
+  if (!last_block(&ctl->counter[2], &flag)) return;
+  const double rm = max_partials(part, gridDim.x, sh);
+  const double vi = max_partials(part + nblk_part, gridDim.x, sh);
+  if (threadIdx.x == 0) {
+    ctl->counter[2] = 0u;
+    ctl->iter += 1;
+    const bool conv = (mode == 0) ? (rm <= (double)ctl->thresh) : (vi == 0.0);
+    if (!isfinite(rm)) {
+      ctl->status = EIK_ERR_BREAKDOWN;
+      ctl->done = 1;
+    } else if (conv || ctl->iter >= ctl->max_iter) {
+      ctl->done = 1;
+    }
+  }
+}
+
+}  // namespace
+
+// ====================================================================== host
+struct MgState {
+  Grid g;
+  CellGrid cg;
+  int px = 0, nblk = 0, cap = 0;
+  std::vector<MgLevel> lv;   // lv[0]: level-0 sizes only
+  float *w = nullptr, *z = nullptr, *p[2] = {nullptr, nullptr}, *q = nullptr;
+  MgCtl *ctl = nullptr, *h_ctl = nullptr;
+  double *part = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  MgFine bound{};            // arrays the graph was captured with
+  int64_t launches = 0;
+};
+
+const char *mg_last_error() { return g_msg.c_str(); }
+int mg_levels(const MgState *mg) { return mg ? (int)mg->lv.size() : 0; }
+int64_t mg_launches(const MgState *mg) { return mg ? mg->launches : 0; }
+
+#define GCK(call)                                                       \
+  do {                                                                  \
+    cudaError_t e_ = (call);                                            \
+    if (e_ != cudaSuccess) {                                            \
+      g_msg = std::string(#call) + ": " + cudaGetErrorString(e_);       \
+      return EIK_ERR_CUDA;                                              \
+    }                                                                   \
+  } while (0)
+
+void mg_destroy(MgState *mg) {
+  if (!mg) return;
+  if (mg->graph) cudaGraphExecDestroy(mg->graph);
+  for (size_t l = 1; l < mg->lv.size(); ++l) {
+    MgLevel &L = mg->lv[l];
+    void *arr[] = {L.a, L.c, L.k, L.g, L.y};
+    for (void *p : arr)
+      if (p) cudaFree(p);
+  }
+  void *arr[] = {mg->w, mg->z, mg->p[0], mg->p[1], mg->q, mg->ctl, mg->part};
+  for (void *p : arr)
+    if (p) cudaFree(p);
+  if (mg->h_ctl) cudaFreeHost(mg->h_ctl);
+  delete mg;
+}
+
+eik_status mg_create(MgState **out, const Grid &g, const CellGrid &cg, int px, int num_sms,
+                     cudaStream_t s) {
+  *out = nullptr;
+  if (g.ndim != 2) {
+    g_msg = "the multigrid inner solve is two-dimensional";
+    return EIK_ERR_ARG;
+  }
+  MgState *mg = new MgState();
+  mg->g = g;
+  mg->cg = cg;
+  mg->px = px;
+  mg->cap = num_sms * 8;
+  const int64_t n = (int64_t)g.nx * g.ny;
+  mg->nblk = (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, mg->cap));
+  MgLevel L0;
+  L0.nx = g.nx;
+  L0.ny = g.ny;
+  mg->lv.push_back(L0);
+  bool ok = true;
+  int nx = g.nx, ny = g.ny;
+  while (ok && (nx > 1 || ny > 1)) {
+    nx = (nx + 1) / 2;
+    ny = (ny + 1) / 2;
+    MgLevel L;
+    L.nx = nx;
+    L.ny = ny;
+    const size_t m = (size_t)nx * ny;
+    ok = cudaMalloc(&L.a, 4 * m) == cudaSuccess && cudaMalloc(&L.c, 16 * m) == cudaSuccess &&
+         cudaMalloc(&L.k, 4 * m) == cudaSuccess && cudaMalloc(&L.g, 4 * m) == cudaSuccess &&
+         cudaMalloc(&L.y, 4 * m) == cudaSuccess;
+    mg->lv.push_back(L);
+  }
+  const size_t np = (size_t)g.ny * px;
+  ok = ok && cudaMalloc(&mg->w, 4 * np) == cudaSuccess && cudaMalloc(&mg->z, 4 * np) == cudaSuccess &&
+       cudaMalloc(&mg->p[0], 4 * np) == cudaSuccess && cudaMalloc(&mg->p[1], 4 * np) == cudaSuccess &&
+       cudaMalloc(&mg->q, 4 * np) == cudaSuccess &&
+       cudaMalloc(&mg->ctl, sizeof(MgCtl)) == cudaSuccess &&
+       cudaMalloc(&mg->part, 2 * sizeof(double) * mg->nblk) == cudaSuccess &&
+       cudaMallocHost(&mg->h_ctl, sizeof(MgCtl)) == cudaSuccess;
+  if (ok) {
+    // padding columns of the pitched arrays are read by no kernel; keep them finite
+    float *arr[] = {mg->w, mg->z, mg->p[0], mg->p[1], mg->q};
+    for (float *a : arr) ok = ok && cudaMemsetAsync(a, 0, 4 * np, s) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(mg->ctl, 0, sizeof(MgCtl), s) == cudaSuccess &&
+         cudaStreamSynchronize(s) == cudaSuccess;
+  }
+  if (!ok) {
+    cudaGetLastError();
+    mg_destroy(mg);
+    g_msg = "multigrid: device allocation failed";
+    return EIK_ERR_OOM;
+  }
+  *out = mg;
+  return EIK_OK;
+}
+
+static int blocks_for(const MgState *mg, int64_t n) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, mg->cap));
+}
+
+eik_status mg_setup(MgState *mg, const MgFine &f, int kmin, cudaStream_t s) {
+  const Grid &g = mg->g;
+  k_mg_weights<<<mg->nblk, kThreads, 0, s>>>(g, mg->cg, mg->px, f.s32, f.kx, f.St, mg->w);
+  MgLevel &L1 = mg->lv[1];
+  k_mg_coarsen0<<<blocks_for(mg, (int64_t)L1.nx * L1.ny), kThreads, 0, s>>>(
+      g, mg->cg, mg->px, f.s32, f.kx, mg->w, L1);
+  mg->launches += 2;
+  for (size_t l = 1; l + 1 < mg->lv.size(); ++l) {
+    MgLevel &C = mg->lv[l + 1];
+    k_mg_coarsen<<<blocks_for(mg, (int64_t)C.nx * C.ny), kThreads, 0, s>>>(mg->lv[l], C);
+    mg->launches++;
+  }
+  GCK(cudaGetLastError());
+  mg->h_ctl->kmin = kmin;
+  return EIK_OK;
+}
+
+// One PCG iteration (direction buffers: read p[set], write p[1 - set]).
+static void launch_iter(MgState *mg, const MgFine &f, int set, cudaStream_t s) {
+  const Grid &g = mg->g;
+  const int L = (int)mg->lv.size() - 1;   // coarsest level index
+  k_mg_down0<<<blocks_for(mg, (int64_t)mg->lv[1].nx * mg->lv[1].ny), kThreads, 0, s>>>(
+      g, mg->cg, mg->px, f.s32, f.kx, mg->w, f.r, mg->lv[1], mg->ctl);
+  for (int l = 1; l < L; ++l)
+    k_mg_down<<<blocks_for(mg, (int64_t)mg->lv[l + 1].nx * mg->lv[l + 1].ny), kThreads, 0, s>>>(
+        mg->lv[l], mg->lv[l + 1], mg->ctl);
+  k_mg_bottom<<<1, kThreads, 0, s>>>(mg->lv[L], mg->ctl);
+  for (int l = L - 1; l >= 1; --l)
+    k_mg_up<<<blocks_for(mg, (int64_t)mg->lv[l].nx * mg->lv[l].ny), kThreads, 0, s>>>(
+        mg->lv[l], mg->lv[l + 1], mg->ctl);
+  k_mg_up0<<<mg->nblk, kThreads, 0, s>>>(g, mg->cg, mg->px, f.s32, f.kx, mg->w, f.r, mg->lv[1],
+                                         mg->z, mg->ctl, mg->part);
+  k_mg_dir<<<mg->nblk, kThreads, 0, s>>>(g, mg->cg, mg->px, f.s32, f.kx, mg->z, mg->p[set],
+                                         mg->p[1 - set], mg->q, mg->ctl, mg->part);
+  k_mg_step<<<mg->nblk, kThreads, 0, s>>>(g, mg->px, mg->p[1 - set], mg->q, f.xref, f.d, f.r,
+                                          mg->ctl, mg->part, mg->nblk);
+}
+
+static int launches_per_iter(const MgState *mg) { return 2 * ((int)mg->lv.size() - 1) + 3; }
+
+eik_status mg_inner(MgState *mg, const MgFine &f, MixCtl *h_st, cudaStream_t s) {
+  if (mg->graph && (f.r != mg->bound.r || f.d != mg->bound.d || f.xref != mg->bound.xref ||
+                    f.s32 != mg->bound.s32 || f.kx != mg->bound.kx)) {
+    cudaGraphExecDestroy(mg->graph);
+    mg->graph = nullptr;
+  }
+  if (!mg->graph) {
+    cudaGraph_t graph;
+    GCK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    for (int it = 0; it < kGraphIters; ++it) launch_iter(mg, f, it & 1, s);
+    GCK(cudaStreamEndCapture(s, &graph));
+    GCK(cudaGraphInstantiate(&mg->graph, graph, 0));
+    GCK(cudaGraphDestroy(graph));
+    mg->bound = f;
+  }
+  MgCtl c{};
+  c.kmin = mg->h_ctl->kmin;
+  c.max_iter = std::max(1, std::min(h_st->max_iter, kMaxInnerIters));
+  c.mode = h_st->mode;
+  c.thresh = h_st->thresh;
+  c.theta = h_st->theta;
+  c.first = 1;
+  *mg->h_ctl = c;
+  GCK(cudaMemcpyAsync(mg->ctl, mg->h_ctl, sizeof(MgCtl), cudaMemcpyHostToDevice, s));
+  for (;;) {
+    GCK(cudaGraphLaunch(mg->graph, s));
+    mg->launches += kGraphIters * launches_per_iter(mg);
+    GCK(cudaMemcpyAsync(mg->h_ctl, mg->ctl, sizeof(MgCtl), cudaMemcpyDeviceToHost, s));
+    GCK(cudaStreamSynchronize(s));
+    if (mg->h_ctl->done) break;
+  }
+  h_st->iter = mg->h_ctl->iter;
+  h_st->status = mg->h_ctl->status;
+  h_st->stalled = mg->h_ctl->stalled;
+  h_st->done = 1;
+  return EIK_OK;
+}
+
+}  // namespace eik

@@ -37,6 +37,7 @@
 #include "eik_batch.h"
 #include "eik_cg32.h"
 #include "eik_launch.h"
+#include "eik_mg.h"
 #include "eik_mixed.h"
 
 namespace eik {
@@ -57,6 +58,10 @@ constexpr int kMaxSweeps = 4;
 constexpr double kInnerReduction = 1e-1;
 constexpr int kMinOverlapBits = 32;    // band overlap (powers of two), at least
 constexpr int kGlobalFinishBits = 160; // ranges that a global refinement still handles
+// multigrid inner solves: sweep only beyond kMgSweepBits, in bands of
+// kMgBandBits (measured: 2048^2 with a 216-bit range converges globally)
+constexpr int kMgSweepBits = 256;
+constexpr int kMgBandBits = 128;
 
 thread_local std::string g_msg = "no error";   // per host thread (batches)
 
@@ -463,6 +468,8 @@ struct MixedState {
   // and inner solves run through it
   BatchExec *batch = nullptr;
   int bidx = -1;
+  // multigrid-preconditioned inner solve (EIK_PRECOND_MULTIGRID), else null
+  MgState *mg = nullptr;
   cudaGraphExec_t graph = nullptr;
   int64_t launches[8] = {0};
   // per-launch CUDA-event timing of the inner passes when profiling
@@ -474,14 +481,15 @@ struct MixedState {
 
 static const char *kMixedNames[] = {"mixed_setup", "coarse_exponents", "mixed_residual64",
                                     "mixed_cg_init", "mixed_cg", "mixed_update",
-                                    "mixed_epilogue", nullptr};
+                                    "mixed_epilogue", "mixed_mg", nullptr};
 
 const char *mixed_kernel_name(int k) {
-  if (k < 0 || k >= 7) return nullptr;
+  if (k < 0 || k >= 8) return nullptr;
   return kMixedNames[k];
 }
 
 int64_t mixed_kernel_launches(const MixedState *m, int k) {
+  if (m && k == 7) return mg_launches(m->mg);
   return (m && k >= 0 && k < 8) ? m->launches[k] : 0;
 }
 
@@ -558,7 +566,7 @@ static bool coarse_smem_attr() {
 }
 
 eik_status mixed_create(MixedState **out, const Grid &g, const TileCount &tc, int num_sms,
-                        int tile_override, cudaStream_t s) {
+                        int tile_override, int precond, cudaStream_t s) {
   MixedState *m = new MixedState();
   mixed_layout(m, g, tc, num_sms);
   // row pitch of the FP32 arrays: a multiple of 4 elements (16-byte rows for
@@ -609,6 +617,14 @@ eik_status mixed_create(MixedState **out, const Grid &g, const TileCount &tc, in
     g_msg = "cannot reserve shared memory for the coarse estimate";
     return EIK_ERR_CUDA;
   }
+  if (precond == EIK_PRECOND_MULTIGRID) {
+    const eik_status ms = mg_create(&m->mg, g, m->cg, m->px, num_sms, s);
+    if (ms != EIK_OK) {
+      g_msg = mg_last_error();
+      mixed_destroy(m);
+      return ms;
+    }
+  }
   *out = m;
   return EIK_OK;
 }
@@ -655,6 +671,7 @@ eik_status mixed_create_member(MixedState **out, const Grid &g, const TileCount 
 
 void mixed_destroy(MixedState *m) {
   if (!m) return;
+  if (m->mg) mg_destroy(m->mg);
   if (m->graph) cudaGraphExecDestroy(m->graph);
   for (auto &e : m->ev)
     if (e) cudaEventDestroy(e);
@@ -777,7 +794,15 @@ static eik_status refine(MixedState *m, const MixedArgs &a, int lo, int hi, int 
     }
     *m->h_st = st;
     MCK(cudaMemcpyAsync(m->st, m->h_st, sizeof(MixCtl), cudaMemcpyHostToDevice, s));
-    if (m->batch) {
+    if (m->mg) {
+      const MgFine fine{m->r32[0], m->d32, m->xref, m->s32, m->kx, m->St};
+      const eik_status ms = mg_inner(m->mg, fine, m->h_st, s);
+      if (ms != EIK_OK) {
+        g_msg = mg_last_error();
+        result = ms;
+        break;
+      }
+    } else if (m->batch) {
       // joins the batch's tile list at its next pass; returns when it ends
       MCK(cudaStreamSynchronize(s));
       const eik_status bs = batch_exec_inner(m->batch, m->bidx, st.seq, m->h_st);
@@ -871,25 +896,39 @@ eik_status mixed_solve(MixedState *m, const MixedArgs &a, int *inner_iters, int 
   m->launches[0] += 3;
   m->launches[1] += 1;
   MCK(cudaGetLastError());
-  if (!m->batch) {
+  if (!m->batch && !m->mg) {
     eik_status gs = build_graph(m, s);
     if (gs != EIK_OK) return gs;
   }
 
-  const int band_bits = (a.opt.band_bits > 0) ? a.opt.band_bits : kBandBits;
+  // multigrid inner solves take wider bands: one global refinement holds
+  // ranges up to kMgSweepBits (its inner products lose the far field only
+  // where their weights 2^(-2 kx) leave the FP64 range)
+  const int band_bits = (a.opt.band_bits > 0) ? a.opt.band_bits : (m->mg ? kMgBandBits : kBandBits);
   int kmin = 0, kmax = 0;
-  if (a.opt.band_bits >= 0) {
+  if (a.opt.band_bits >= 0 || m->mg) {
     std::vector<int> hk(m->cg.ncell);
     MCK(cudaMemcpyAsync(hk.data(), m->kx, sizeof(int) * hk.size(), cudaMemcpyDeviceToHost, s));
     MCK(cudaStreamSynchronize(s));
     kmin = *std::min_element(hk.begin(), hk.end());
     kmax = *std::max_element(hk.begin(), hk.end());
   }
+  // the multigrid hierarchy follows the coefficients of the current band
+  auto mg_rebuild = [&](int klo) -> eik_status {
+    if (!m->mg) return EIK_OK;
+    const MgFine fine{m->r32[0], m->d32, m->xref, m->s32, m->kx, m->St};
+    const eik_status ms = mg_setup(m->mg, fine, std::max(klo, kmin), s);
+    if (ms != EIK_OK) g_msg = mg_last_error();
+    return ms;
+  };
   const int max_outer = (a.opt.max_outer > 0) ? a.opt.max_outer : 30;
   int total = 0, outer = 0;
   eik_status result;
-  const int sweep_bits = (a.opt.band_bits > 0) ? 2 * a.opt.band_bits : kSweepBits;
+  const int sweep_bits = (a.opt.band_bits > 0) ? 2 * a.opt.band_bits
+                                               : (m->mg ? kMgSweepBits : kSweepBits);
   if (a.opt.band_bits < 0 || kmax - kmin <= sweep_bits) {
+    const eik_status ms = mg_rebuild(kmin);
+    if (ms != EIK_OK) return ms;
     result = refine(m, a, INT_MIN, INT_MAX, max_outer, &total, &outer, res_cw, trace);
   } else {
     // Level-set sweep: bands of band_bits powers of two in kx (plus an outer
@@ -908,6 +947,8 @@ eik_status mixed_solve(MixedState *m, const MixedArgs &a, int *inner_iters, int 
                                                       m->s32);
         m->launches[0]++;
         MCK(cudaGetLastError());
+        const eik_status ms = mg_rebuild(lo);
+        if (ms != EIK_OK) return ms;
         if (trace) fprintf(stderr, "[mixed] sweep %d band [%d, %d)\n", sweep, lo, hi);
         const eik_status bs = refine(m, a, lo, hi, max_outer, &total, &outer, res_cw, trace);
         if (bs != EIK_OK && bs != EIK_ERR_NOT_CONVERGED) return bs;   // breakdown, timeout, CUDA
@@ -915,6 +956,8 @@ eik_status mixed_solve(MixedState *m, const MixedArgs &a, int *inner_iters, int 
       }
       k_sig32<<<blocks(g.n), kThreads, 0, s>>>(g.n, g.nx, m->px, a.sig, m->s32);
       m->launches[0]++;
+      const eik_status ms = mg_rebuild(kmin);
+      if (ms != EIK_OK) return ms;
       int checks = 0;
       result = refine(m, a, INT_MIN, INT_MAX, 0, &total, &checks, res_cw, trace);
       if (result == EIK_OK || total >= a.opt.max_iter) break;

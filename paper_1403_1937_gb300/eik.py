@@ -62,7 +62,7 @@ def make_options(precision: str = "fp64", tol: Optional[float] = None,
                  boundary: str = "half_cell", inner_tol: float = 0.0,
                  max_outer: int = 0, tile_override: int = 0,
                  band_bits: int = 0, test_flags: int = 0, batch_pack: int = 0,
-                 batch_tile_rows: int = 0) -> _lib.Options:
+                 batch_tile_rows: int = 0, precond="jacobi") -> _lib.Options:
     o = _lib.default_options()
     o.precision = {"fp64": _lib.PREC_FP64, "mixed": _lib.PREC_MIXED}[precision]
     if tol is not None:
@@ -80,6 +80,8 @@ def make_options(precision: str = "fp64", tol: Optional[float] = None,
     o.test_flags = int(test_flags)
     o.batch_pack = int(batch_pack)
     o.batch_tile_rows = int(batch_tile_rows)
+    o.precond = (precond if isinstance(precond, int) else
+                 {"jacobi": _lib.PRECOND_JACOBI, "multigrid": _lib.PRECOND_MULTIGRID}[precond])
     return o
 
 

@@ -91,6 +91,25 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.eik_destroy(None) == _lib.EIK_OK
 
 
+def test_preconditioner_option_checked_without_gpu(lib):
+    """An unknown precond, multigrid in FP64 and multigrid on a 3D grid are
+    rejected before any CUDA call."""
+    from paper_1403_1937_gb300 import _lib
+    P = ctypes.c_void_p(0x1000)      # never dereferenced: the checks fail first
+    for ndim, prec, pc in ((2, _lib.PREC_MIXED, 2), (2, _lib.PREC_MIXED, -1),
+                           (2, _lib.PREC_FP64, _lib.PRECOND_MULTIGRID),
+                           (3, _lib.PREC_MIXED, _lib.PRECOND_MULTIGRID)):
+        o = _lib.default_options()
+        o.precision = prec
+        o.precond = pc
+        dims = (ctypes.c_int64 * ndim)(*([9] * ndim))
+        out = ctypes.c_void_p()
+        st = lib.eik_create(ctypes.byref(out), ndim, dims, 0.1, 0.1, P, P, None, 1,
+                            ctypes.byref(o), None)
+        assert st == _lib.EIK_ERR_ARG, (ndim, prec, pc)
+        assert "precond" in _lib.last_error() or "multigrid" in _lib.last_error()
+
+
 def test_path_and_forcing_entry_points_validate_arguments_without_gpu(lib):
     """Argument checks of the path-planning, forcing and allocation-free
     entry points run before any CUDA call."""
