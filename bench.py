@@ -48,6 +48,14 @@ ALGO_BYTES_PER_NODE = {
     # xref (f32)
     "mixed_residual64": 32,
     "mixed_update": 20,  # read d (f32), read and write x (f64)
+    # one multigrid-preconditioned inner iteration (all its kernels), level 0:
+    # V-cycle down (read r, sig, w; write the level-1 residual, 1/4 per
+    # node) 13 B, V-cycle up (read r, sig, w, the level-1 correction; write
+    # z) 17 B, direction (read z, p, sig; write p, q) 20 B, step (read p, q,
+    # d, r; write d, r) 24 B; the coarse levels (read g, a, 4 coefficients,
+    # k; write the next residual / read them again plus the parent
+    # correction, write y: ~62 B per coarse node, n/3 coarse nodes) ~21 B
+    "mixed_mg": 95,
 }
 
 # The FP64 passes are bound by the FP64 pipe, not by HBM: their roofline is
@@ -89,9 +97,15 @@ def parse():
     ap.add_argument("--tile-override", type=int, default=0,
                     help="inner-CG kernel variant (eik_options.tile_override): 0 library "
                          "choice, 1..4 the variants listed in include/eik.h")
-    ap.add_argument("--modes", default="both", choices=["both", "one"],
+    ap.add_argument("--mg-tol", type=float, default=1e-7,
+                    help="componentwise tolerance of the multigrid-preconditioned "
+                         "mode (2D single grids; at 1e-6 its S error can exceed 1e-6)")
+    ap.add_argument("--no-mg", action="store_true",
+                    help="skip the multigrid-preconditioned mode on 2D workloads")
+    ap.add_argument("--modes", default="both", choices=["both", "one", "mg"],
                     help="single-grid workloads: time both precision modes (default) or only "
-                         "--precision (shorter profiler captures)")
+                         "--precision (shorter profiler captures); mg: only the "
+                         "multigrid-preconditioned mixed mode (2D)")
     ap.add_argument("--batch-pack", type=int, default=0, choices=[-1, 0, 1],
                     help="batched workload: 0/1 packed (one launch per pass over all "
                          "instances), -1 each instance on its own stream")
@@ -300,15 +314,24 @@ def measure(args, wname, ws, local, modes=None):
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
 
-    def make(prec):
-        opt = eik.make_options(precision=prec, tol=args.tol, tile_override=args.tile_override,
-                               band_bits=args.band_bits, inner_tol=args.inner_tol)
+    def make(mode):
+        if mode == "mixed_mg":    # multigrid-preconditioned inner solve (2D)
+            opt = eik.make_options(precision="mixed", tol=args.mg_tol, precond="multigrid",
+                                   band_bits=args.band_bits, inner_tol=args.inner_tol)
+        else:
+            opt = eik.make_options(precision=mode, tol=args.tol,
+                                   tile_override=args.tile_override,
+                                   band_bits=args.band_bits, inner_tol=args.inner_tol)
         return eik.eik_create(inst.dims, inst.h, inst.hbar, f_dev, src, None, opt)
 
+    if modes is None and args.modes == "mg":
+        modes = ["mixed_mg"]
     if modes is None:
         modes = [args.precision]
         if args.modes == "both":
             modes += [m for m in ("fp64", "mixed") if m != args.precision]
+        if len(inst.dims) == 2 and not args.no_mg:
+            modes.append("mixed_mg")
     results = {}
     S_dev = torch.empty(inst.dims[::-1], dtype=torch.float64, device="cuda")
     for mode in modes:
@@ -581,7 +604,7 @@ def run_batch(args, emit=True):
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1e3 * total / args.steps, 3), "higher_is_better": True,
             "scaling": "strong", "vs_baseline": None,
-            "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+            "dtype": "f64" if head_mode == "fp64" else "f32+f64", "data": "synthetic",
             "config": {"workload": f"batched 2D: {len(all_insts)} instances, sides 64..1024, "
                                    "Fourier f in [0.5,1.5], 1-8 sources, hbar in {2h,4h,8h}",
                        "instances": len(all_insts), "instances_rank0": len(insts),
@@ -785,10 +808,11 @@ def run_paths(args):
     print(json.dumps(line), flush=True)
 
 
-def roofline(res, inst, wname):
+def roofline(res, inst, wname, only=None):
     peak, peak_src = measured_peaks()
     km = {k: v for k, v in res["kernel_ms"].items() if v[0] is not None}
-    cand = {k: v for k, v in km.items() if k in ALGO_BYTES_PER_NODE}
+    cand = {k: v for k, v in km.items() if k in ALGO_BYTES_PER_NODE and
+            (only is None or k == only) and (only is not None or k != "mixed_mg")}
     if not cand:
         return None
     dom = max(cand, key=lambda k: cand[k][2])
@@ -913,7 +937,8 @@ def main():
         batch_blocks = other_blocks(args)
     if rank != 0:
         return
-    head = results.get(args.precision, {})
+    head_mode = "mixed_mg" if args.modes == "mg" else args.precision
+    head = results.get(head_mode, {})
     if "glups" not in head:
         print(json.dumps({"metric": METRIC, "error": head.get("error", "failed")}), flush=True)
         sys.exit(1)
@@ -932,20 +957,33 @@ def main():
     if "glups" in results.get("fp64", {}) and "glups" in results.get("mixed", {}):
         comparison["mixed_speedup_vs_fp64"] = round(
             results["fp64"]["ms_per_step"] / results["mixed"]["ms_per_step"], 3)
+    mg = results.get("mixed_mg", {})
+    if "glups" in mg:
+        # time to solution of the multigrid-preconditioned mixed solve; its
+        # GLUPS counts multigrid iterations, so the comparison is by time
+        comparison["mixed_mg"]["tol_componentwise"] = args.mg_tol
+        comparison["mixed_mg"]["roofline_iteration"] = roofline(mg, inst, args.workload,
+                                                                only="mixed_mg")
+        for ref in ("fp64", "mixed"):
+            if "glups" in results.get(ref, {}):
+                comparison[f"mixed_mg_speedup_vs_{ref}"] = round(
+                    results[ref]["ms_per_step"] / mg["ms_per_step"], 3)
     line = {
         "metric": METRIC, "value": round(head["glups"], 4), "unit": UNIT,
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(head["ms_per_step"], 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "dtype": "f64" if head_mode == "fp64" else "f32+f64",
         "data": "synthetic",
-        "config": dict(desc, precision=args.precision, tol_componentwise=args.tol,
+        "config": dict(desc, precision=head_mode,
+                       tol_componentwise=args.mg_tol if head_mode == "mixed_mg" else args.tol,
                        l2="flushed between steps (256 MiB write)",
                        parallelism="replicas" if ws > 1 else "single GPU"),
         "e2e": head.get("e2e"),
         "gpu_launches": head["gpu_launches"],
         "clocks": head["clocks"],
-        "roofline": roofline(head, inst, args.workload),
+        "roofline": roofline(head, inst, args.workload,
+                             only="mixed_mg" if head_mode == "mixed_mg" else None),
         "cpu_baseline": cpu,
         "comparison": comparison,
         "kernels": kernel_table(head, inst),

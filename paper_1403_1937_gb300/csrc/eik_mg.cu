@@ -70,6 +70,7 @@ thread_local std::string g_msg = "no error";
 struct MgLevel {
   int nx = 0, ny = 0;
   float *a = nullptr;            // diagonal; a < 0 marks a node with no unknowns
+  float *ia = nullptr;           // 1 / a (0 on nodes with no unknowns)
   float *c = nullptr;            // 4 x nx*ny row-relative coefficients: W, E, S, N
   int *k = nullptr;
   float *g = nullptr, *y = nullptr;
@@ -90,21 +91,46 @@ __device__ __forceinline__ int kx_at(const CellGrid &cg, int x, int y, const int
 __device__ __forceinline__ float face(int i, int n, int boundary) {
   return (boundary == EIK_BOUNDARY_HALF_CELL && (i == 0 || i == n - 1)) ? 0.5f : 1.f;
 }
-__device__ __forceinline__ float p2f(int e) { return ldexpf(1.f, e); }
+// 2^e from its bit pattern; 0 below the normal range (such factors only
+// scale terms that are negligible), e capped at 127.
+__device__ __forceinline__ float p2f(int e) {
+  e = min(e, 127);
+  return (e < -126) ? 0.f : __int_as_float((e + 127) << 23);
+}
+
+// Grid-stride loops over the rows (blockIdx.y) and columns (x) of a level:
+// no 64-bit division per node.
+#define MG_ROWS(ny_) for (int y = blockIdx.y; y < (ny_); y += gridDim.y)
+#define MG_COLS(nx_) \
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < (nx_); x += gridDim.x * blockDim.x)
 
 // Level-0 off-diagonal sum  sig_i sum_j omega_ij sig_j 2^(k_i - k_j) v(j)
-// for the node (x, y), v given by a functor of the pitched index.
+// for the node (x, y); v(j, xj, yj) gives the vector at pitched index j.
+// The exponent is looked up only where the neighbour lies in another cell.
 template <class V>
 __device__ __forceinline__ float nb0(const Grid &g, const CellGrid &cg, int px,
                                      const float *__restrict__ s32, const int *__restrict__ kx,
                                      int x, int y, int ki, V v) {
   float acc = 0.f;
+  const int mask = cg.B - 1;
   const float hy = face(y, g.ny, g.boundary), hx = face(x, g.nx, g.boundary);
   const int64_t i = (int64_t)y * px + x;
-  if (x > 0) acc += hy * s32[i - 1] * p2f(ki - kx_at(cg, x - 1, y, kx)) * v(i - 1);
-  if (x + 1 < g.nx) acc += hy * s32[i + 1] * p2f(ki - kx_at(cg, x + 1, y, kx)) * v(i + 1);
-  if (y > 0) acc += hx * s32[i - px] * p2f(ki - kx_at(cg, x, y - 1, kx)) * v(i - px);
-  if (y + 1 < g.ny) acc += hx * s32[i + px] * p2f(ki - kx_at(cg, x, y + 1, kx)) * v(i + px);
+  if (x > 0) {
+    const float f = ((x & mask) == 0) ? p2f(ki - kx_at(cg, x - 1, y, kx)) : 1.f;
+    acc = fmaf(hy * s32[i - 1] * f, v(i - 1, x - 1, y), acc);
+  }
+  if (x + 1 < g.nx) {
+    const float f = (((x + 1) & mask) == 0) ? p2f(ki - kx_at(cg, x + 1, y, kx)) : 1.f;
+    acc = fmaf(hy * s32[i + 1] * f, v(i + 1, x + 1, y), acc);
+  }
+  if (y > 0) {
+    const float f = ((y & mask) == 0) ? p2f(ki - kx_at(cg, x, y - 1, kx)) : 1.f;
+    acc = fmaf(hx * s32[i - px] * f, v(i - px, x, y - 1), acc);
+  }
+  if (y + 1 < g.ny) {
+    const float f = (((y + 1) & mask) == 0) ? p2f(ki - kx_at(cg, x, y + 1, kx)) : 1.f;
+    acc = fmaf(hx * s32[i + px] * f, v(i + px, x, y + 1), acc);
+  }
   return s32[i] * acc;
 }
 
@@ -217,6 +243,7 @@ __global__ void k_mg_coarsen0(Grid g, CellGrid cg, int px, const float *__restri
       cN *= f;
     }
     L.a[t] = live ? (float)A : -1.f;
+    L.ia[t] = live ? (float)(1.0 / A) : 0.f;
     L.c[kW * m + t] = live ? (float)cW : 0.f;
     L.c[kE * m + t] = live ? (float)cE : 0.f;
     L.c[kS * m + t] = live ? (float)cS : 0.f;
@@ -248,6 +275,7 @@ __global__ void k_mg_coarsen(MgLevel F, MgLevel C) {
     const int kc = box_k(F, X, Y);
     if (kc == INT_MAX) {
       C.a[t] = -1.f;
+      C.ia[t] = 0.f;
       for (int d = 0; d < 4; ++d) C.c[d * m + t] = 0.f;
       C.k[t] = F.k[(int64_t)(2 * Y) * F.nx + 2 * X];
       continue;
@@ -269,6 +297,7 @@ __global__ void k_mg_coarsen(MgLevel F, MgLevel C) {
         A += r * row;
       }
     C.a[t] = (float)A;
+    C.ia[t] = (float)(1.0 / A);
     C.c[kW * m + t] = (X > 0) ? (float)cW : 0.f;
     C.c[kE * m + t] = (X + 1 < C.nx) ? (float)cE : 0.f;
     C.c[kS * m + t] = (Y > 0) ? (float)cS : 0.f;
@@ -283,81 +312,131 @@ __global__ void k_mg_down0(Grid g, CellGrid cg, int px, const float *__restrict_
                            const int *__restrict__ kx, const float *__restrict__ w,
                            const float *__restrict__ r, MgLevel L1, const MgCtl *ctl) {
   if (ctl->done) return;
-  const int64_t n = (int64_t)L1.nx * L1.ny;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int X = (int)(t % L1.nx), Y = (int)(t / L1.nx);
+  auto rv = [&](int64_t j, int, int) { return r[j]; };
+  MG_ROWS(L1.ny) MG_COLS(L1.nx) {
+    const int X = x, Y = y;
     float sum = 0.f;
-    for (int y = 2 * Y; y <= min(2 * Y + 1, g.ny - 1); ++y)
-      for (int x = 2 * X; x <= min(2 * X + 1, g.nx - 1); ++x) {
-        const int64_t i = (int64_t)y * px + x;
+    for (int yy = 2 * Y; yy <= min(2 * Y + 1, g.ny - 1); ++yy)
+      for (int xx = 2 * X; xx <= min(2 * X + 1, g.nx - 1); ++xx) {
+        const int64_t i = (int64_t)yy * px + xx;
         const float wi = w[i];
         if (wi == 0.f) continue;
-        const int ki = kx_at(cg, x, y, kx);
-        const float off = nb0(g, cg, px, s32, kx, x, y, ki, [&](int64_t j) { return r[j]; });
+        const int ki = kx_at(cg, xx, yy, kx);
+        const float off = nb0(g, cg, px, s32, kx, xx, yy, ki, rv);
         // (A (omega r))_i = omega (r_i - off)
         const float ti = r[i] - kOmega * (r[i] - off);
         sum = fmaf(wi, ti, sum);
       }
-    L1.g[t] = sum;
+    L1.g[(int64_t)Y * L1.nx + X] = sum;
   }
 }
 
-// Level l down (l >= 1): y = omega g / a, t = g - A y, restricted to l + 1.
+// Level l down (l >= 1) at coarse node (x, y): y = omega g / a on the box,
+// t = g - A y, restricted to level l + 1.
+__device__ __forceinline__ void down_node(const MgLevel &F, const MgLevel &C, int x, int y) {
+  auto yv = [&](int64_t j) { return kOmega * F.g[j] * F.ia[j]; };
+  const int64_t t = (int64_t)y * C.nx + x;
+  const int kc = C.k[t];
+  float sum = 0.f;
+  if (C.a[t] >= 0.f) {
+    for (int yy = 2 * y; yy <= min(2 * y + 1, F.ny - 1); ++yy)
+      for (int xx = 2 * x; xx <= min(2 * x + 1, F.nx - 1); ++xx) {
+        const int64_t i = (int64_t)yy * F.nx + xx;
+        if (F.a[i] < 0.f) continue;
+        const float ti = F.g[i] - apply_l(F, xx, yy, yv);
+        sum = fmaf(p2f(2 * (kc - F.k[i])), ti, sum);
+      }
+  }
+  C.g[t] = sum;
+}
+
 __global__ void k_mg_down(MgLevel F, MgLevel C, const MgCtl *ctl) {
   if (ctl->done) return;
-  const int64_t n = (int64_t)C.nx * C.ny;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int X = (int)(t % C.nx), Y = (int)(t / C.nx);
-    const int kc = C.k[t];
-    float sum = 0.f;
-    if (C.a[t] >= 0.f) {
-      auto yv = [&](int64_t j) { return kOmega * F.g[j] / fabsf(F.a[j]); };
-      for (int y = 2 * Y; y <= min(2 * Y + 1, F.ny - 1); ++y)
-        for (int x = 2 * X; x <= min(2 * X + 1, F.nx - 1); ++x) {
-          const int64_t i = (int64_t)y * F.nx + x;
-          if (F.a[i] < 0.f) continue;
-          const float ti = F.g[i] - apply_l(F, x, y, yv);
-          sum = fmaf(p2f(2 * (kc - F.k[i])), ti, sum);
-        }
+  MG_ROWS(C.ny) MG_COLS(C.nx) down_node(F, C, x, y);
+}
+
+// Level l up (l >= 1) at node (x, y): u = omega g / a + y(parent);
+// y = u + omega (g - A u) / a.
+__device__ __forceinline__ void up_node(const MgLevel &F, const MgLevel &C, int x, int y) {
+  {
+    const int64_t t = (int64_t)y * F.nx + x;
+    if (F.a[t] < 0.f) {
+      F.y[t] = 0.f;
+      return;
     }
-    C.g[t] = sum;
+    // u at the node (xj, yj) = index j of this level
+    auto uat = [&](int64_t j, int xj, int yj) {
+      const float par = (F.a[j] >= 0.f) ? C.y[(int64_t)(yj >> 1) * C.nx + (xj >> 1)] : 0.f;
+      return fmaf(kOmega * F.g[j], F.ia[j], par);
+    };
+    const int64_t m = (int64_t)F.nx * F.ny;
+    const float ut = uat(t, x, y);
+    float Au = fabsf(F.a[t]) * ut;
+    if (x > 0) Au = fmaf(F.c[kW * m + t], uat(t - 1, x - 1, y), Au);
+    if (x + 1 < F.nx) Au = fmaf(F.c[kE * m + t], uat(t + 1, x + 1, y), Au);
+    if (y > 0) Au = fmaf(F.c[kS * m + t], uat(t - F.nx, x, y - 1), Au);
+    if (y + 1 < F.ny) Au = fmaf(F.c[kN * m + t], uat(t + F.nx, x, y + 1), Au);
+    F.y[t] = fmaf(kOmega * (F.g[t] - Au), F.ia[t], ut);
   }
 }
 
-// Coarsest level (one node per axis or a few): exact for a single node,
-// otherwise a damped-Jacobi sweep.
-__global__ void k_mg_bottom(MgLevel L, const MgCtl *ctl) {
-  if (ctl->done) return;
-  const int64_t n = (int64_t)L.nx * L.ny;
-  for (int64_t t = threadIdx.x; t < n; t += blockDim.x)
-    L.y[t] = (L.a[t] >= 0.f) ? L.g[t] / L.a[t] : 0.f;
-}
-
-// Level l up (l >= 1): u = omega g / a + y(parent); y = u + omega (g - A u) / a.
 __global__ void k_mg_up(MgLevel F, MgLevel C, const MgCtl *ctl) {
   if (ctl->done) return;
-  const int64_t n = (int64_t)F.nx * F.ny;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(t % F.nx), y = (int)(t / F.nx);
-    if (F.a[t] < 0.f) {
-      F.y[t] = 0.f;
-      continue;
-    }
-    auto u = [&](int64_t j) {
-      const int xj = (int)(j % F.nx), yj = (int)(j / F.nx);
-      const float par = (F.a[j] >= 0.f) ? C.y[(int64_t)(yj >> 1) * C.nx + (xj >> 1)] : 0.f;
-      return kOmega * F.g[j] / fabsf(F.a[j]) + par;
-    };
-    const float ut = u(t);
-    F.y[t] = ut + kOmega * (F.g[t] - apply_l(F, x, y, u)) / F.a[t];
+  MG_ROWS(F.ny) MG_COLS(F.nx) up_node(F, C, x, y);
+}
+
+// The small levels s .. L of the V-cycle in one block: down sweeps, the
+// single-node solve, up sweeps, a block barrier between levels.
+constexpr int kMaxLevels = 24;
+constexpr int kTailNodes = 256;    // levels of at most this many nodes run in the tail
+constexpr int kTailThreads = 1024;
+struct MgTail {
+  MgLevel lv[kMaxLevels];
+  int s, L;
+};
+__global__ void __launch_bounds__(kTailThreads) k_mg_tail(MgTail T, const MgCtl *ctl) {
+  if (ctl->done) return;
+  for (int l = T.s; l < T.L; ++l) {
+    const MgLevel &F = T.lv[l], &C = T.lv[l + 1];
+    for (int t = threadIdx.x; t < C.nx * C.ny; t += blockDim.x) down_node(F, C, t % C.nx, t / C.nx);
+    __syncthreads();
+  }
+  {
+    const MgLevel &B = T.lv[T.L];
+    for (int t = threadIdx.x; t < B.nx * B.ny; t += blockDim.x)
+      B.y[t] = B.g[t] * B.ia[t];
+    __syncthreads();
+  }
+  for (int l = T.L - 1; l >= T.s; --l) {
+    const MgLevel &F = T.lv[l], &C = T.lv[l + 1];
+    for (int t = threadIdx.x; t < F.nx * F.ny; t += blockDim.x) up_node(F, C, t % F.nx, t / F.nx);
+    __syncthreads();
   }
 }
 
 // ------------------------------------------------------------- PCG passes
-__device__ __forceinline__ double wdot(int k, int kmin) { return ldexp(1.0, 2 * (kmin - k)); }
+// Inner-product weight 2^(-2 (k - kmin)); 0 past the FP32 range, where a
+// term is below 2^-126 of the nearest ones.  Per-thread sums are FP32, the
+// block and grid sums FP64.
+__device__ __forceinline__ float wdot(int k, int kmin) { return p2f(2 * (kmin - k)); }
+
+__device__ __forceinline__ int block_id() { return blockIdx.y * gridDim.x + blockIdx.x; }
+__device__ __forceinline__ int block_count() { return gridDim.x * gridDim.y; }
+
+// Last-block-done over a 2D grid (all gridDim.x * gridDim.y blocks): true in
+// the block that arrives last, after every block has written its partials.
+__device__ __forceinline__ bool last_block_2d(unsigned int *ticket, int *sh_flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int t = atomicAdd(ticket, 1u);
+    *sh_flag = (t == (unsigned int)block_count() - 1u);
+  }
+  __syncthreads();
+  const bool last = *sh_flag != 0;
+  if (last) __threadfence();
+  return last;
+}
 
 // Level 0 up: u = omega r + w y1(parent), z = u + omega (r - A u); rho = <r, z>.
 __global__ void __launch_bounds__(kThreads)
@@ -368,31 +447,27 @@ k_mg_up0(Grid g, CellGrid cg, int px, const float *__restrict__ s32, const int *
   __shared__ int flag;
   if (ctl->done) return;
   const int kmin = ctl->kmin;
-  const int64_t n = (int64_t)g.nx * g.ny;
-  double rz = 0.0;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(t % g.nx), y = (int)(t / g.nx);
+  float rz = 0.f;
+  auto u = [&](int64_t j, int xj, int yj) {
+    return fmaf(w[j], L1.y[(int64_t)(yj >> 1) * L1.nx + (xj >> 1)], kOmega * r[j]);
+  };
+  MG_ROWS(g.ny) MG_COLS(g.nx) {
     const int64_t i = (int64_t)y * px + x;
     if (s32[i] == 0.f) {
       z[i] = 0.f;
       continue;
     }
-    auto u = [&](int64_t j) {
-      const int yj = (int)(j / px), xj = (int)(j - (int64_t)yj * px);
-      return kOmega * r[j] + w[j] * L1.y[(int64_t)(yj >> 1) * L1.nx + (xj >> 1)];
-    };
     const int ki = kx_at(cg, x, y, kx);
-    const float ui = u(i);
+    const float ui = u(i, x, y);
     const float Au = ui - nb0(g, cg, px, s32, kx, x, y, ki, u);
-    const float zi = ui + kOmega * (r[i] - Au);
+    const float zi = fmaf(kOmega, r[i] - Au, ui);
     z[i] = zi;
-    rz += (double)r[i] * (double)zi * wdot(ki, kmin);
+    rz = fmaf(r[i] * zi, wdot(ki, kmin), rz);
   }
-  const double bs = block_sum(rz, sh);
-  if (threadIdx.x == 0) part[blockIdx.x] = bs;
-  if (!last_block(&ctl->counter[0], &flag)) return;
-  const double tot = sum_partials(part, gridDim.x, sh);
+  const double bs = block_sum((double)rz, sh);
+  if (threadIdx.x == 0) part[block_id()] = bs;
+  if (!last_block_2d(&ctl->counter[0], &flag)) return;
+  const double tot = sum_partials(part, block_count(), sh);
   if (threadIdx.x == 0) {
     ctl->beta = ctl->first ? 0.0 : tot / ctl->rho;
     ctl->rho = tot;
@@ -415,27 +490,24 @@ k_mg_dir(Grid g, CellGrid cg, int px, const float *__restrict__ s32, const int *
   const int kmin = ctl->kmin;
   const float beta = (float)ctl->beta;
   const bool first = ctl->first != 0;
-  const int64_t n = (int64_t)g.nx * g.ny;
-  double pq = 0.0;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(t % g.nx), y = (int)(t / g.nx);
+  float pq = 0.f;
+  auto pv = [&](int64_t j, int, int) { return first ? z[j] : fmaf(beta, p_old[j], z[j]); };
+  MG_ROWS(g.ny) MG_COLS(g.nx) {
     const int64_t i = (int64_t)y * px + x;
-    auto pv = [&](int64_t j) { return first ? z[j] : fmaf(beta, p_old[j], z[j]); };
-    const float pi = pv(i);
+    const float pi = pv(i, x, y);
     float qi = 0.f;
     if (s32[i] != 0.f) {
       const int ki = kx_at(cg, x, y, kx);
       qi = pi - nb0(g, cg, px, s32, kx, x, y, ki, pv);
-      pq += (double)pi * (double)qi * wdot(ki, kmin);
+      pq = fmaf(pi * qi, wdot(ki, kmin), pq);
     }
     p_new[i] = pi;
     q[i] = qi;
   }
-  const double bs = block_sum(pq, sh);
-  if (threadIdx.x == 0) part[blockIdx.x] = bs;
-  if (!last_block(&ctl->counter[1], &flag)) return;
-  const double tot = sum_partials(part, gridDim.x, sh);
+  const double bs = block_sum((double)pq, sh);
+  if (threadIdx.x == 0) part[block_id()] = bs;
+  if (!last_block_2d(&ctl->counter[1], &flag)) return;
+  const double tot = sum_partials(part, block_count(), sh);
   if (threadIdx.x == 0) {
     ctl->counter[1] = 0u;
     ctl->first = 0;
@@ -460,28 +532,25 @@ k_mg_step(Grid g, int px, const float *__restrict__ p, const float *__restrict__
   const float alpha = (float)ctl->alpha;
   const int mode = ctl->mode;
   const float theta = ctl->theta;
-  const int64_t n = (int64_t)g.nx * g.ny;
-  double rmax = 0.0, viol = 0.0;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(t % g.nx), y = (int)(t / g.nx);
+  float rmax = 0.f, viol = 0.f;
+  MG_ROWS(g.ny) MG_COLS(g.nx) {
     const int64_t i = (int64_t)y * px + x;
     const float di = fmaf(alpha, p[i], d[i]);
     const float ri = fmaf(-alpha, q[i], r[i]);
     d[i] = di;
     r[i] = ri;
-    rmax = fmax(rmax, (double)fabsf(ri));
-    if (mode == 1 && fabsf(ri) > theta * fabsf(xref[i] + di)) viol = 1.0;
+    rmax = fmaxf(rmax, fabsf(ri));
+    if (mode == 1 && fabsf(ri) > theta * fabsf(xref[i] + di)) viol = 1.f;
   }
-  const double b1 = block_max(rmax, sh);
-  const double b2 = block_max(viol, sh);
+  const double b1 = block_max((double)rmax, sh);
+  const double b2 = block_max((double)viol, sh);
   if (threadIdx.x == 0) {
-    part[blockIdx.x] = b1;
-    part[nblk_part + blockIdx.x] = b2;
+    part[block_id()] = b1;
+    part[nblk_part + block_id()] = b2;
   }
-  if (!last_block(&ctl->counter[2], &flag)) return;
-  const double rm = max_partials(part, gridDim.x, sh);
-  const double vi = max_partials(part + nblk_part, gridDim.x, sh);
+  if (!last_block_2d(&ctl->counter[2], &flag)) return;
+  const double rm = max_partials(part, block_count(), sh);
+  const double vi = max_partials(part + nblk_part, block_count(), sh);
   if (threadIdx.x == 0) {
     ctl->counter[2] = 0u;
     ctl->iter += 1;
@@ -509,11 +578,28 @@ struct MgState {
   cudaGraphExec_t graph = nullptr;
   MgFine bound{};            // arrays the graph was captured with
   int64_t launches = 0;
+  bool profile = false;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  int64_t timed_iters = 0;
+  double ms = 0.0;
 };
 
 const char *mg_last_error() { return g_msg.c_str(); }
 int mg_levels(const MgState *mg) { return mg ? (int)mg->lv.size() : 0; }
 int64_t mg_launches(const MgState *mg) { return mg ? mg->launches : 0; }
+void mg_set_profiling(MgState *mg, bool on) {
+  if (mg) mg->profile = on;
+}
+void mg_time(const MgState *mg, int64_t *iters, double *ms) {
+  *iters = mg ? mg->timed_iters : 0;
+  *ms = mg ? mg->ms : 0.0;
+}
+void mg_reset(MgState *mg) {
+  if (!mg) return;
+  mg->launches = 0;
+  mg->timed_iters = 0;
+  mg->ms = 0.0;
+}
 
 #define GCK(call)                                                       \
   do {                                                                  \
@@ -527,9 +613,11 @@ int64_t mg_launches(const MgState *mg) { return mg ? mg->launches : 0; }
 void mg_destroy(MgState *mg) {
   if (!mg) return;
   if (mg->graph) cudaGraphExecDestroy(mg->graph);
+  for (auto &e : mg->ev)
+    if (e) cudaEventDestroy(e);
   for (size_t l = 1; l < mg->lv.size(); ++l) {
     MgLevel &L = mg->lv[l];
-    void *arr[] = {L.a, L.c, L.k, L.g, L.y};
+    void *arr[] = {L.a, L.ia, L.c, L.k, L.g, L.y};
     for (void *p : arr)
       if (p) cudaFree(p);
   }
@@ -560,14 +648,15 @@ eik_status mg_create(MgState **out, const Grid &g, const CellGrid &cg, int px, i
   mg->lv.push_back(L0);
   bool ok = true;
   int nx = g.nx, ny = g.ny;
-  while (ok && (nx > 1 || ny > 1)) {
+  while (ok && (nx > 1 || ny > 1) && (int)mg->lv.size() < kMaxLevels) {
     nx = (nx + 1) / 2;
     ny = (ny + 1) / 2;
     MgLevel L;
     L.nx = nx;
     L.ny = ny;
     const size_t m = (size_t)nx * ny;
-    ok = cudaMalloc(&L.a, 4 * m) == cudaSuccess && cudaMalloc(&L.c, 16 * m) == cudaSuccess &&
+    ok = cudaMalloc(&L.a, 4 * m) == cudaSuccess && cudaMalloc(&L.ia, 4 * m) == cudaSuccess &&
+         cudaMalloc(&L.c, 16 * m) == cudaSuccess &&
          cudaMalloc(&L.k, 4 * m) == cudaSuccess && cudaMalloc(&L.g, 4 * m) == cudaSuccess &&
          cudaMalloc(&L.y, 4 * m) == cudaSuccess;
     mg->lv.push_back(L);
@@ -577,7 +666,7 @@ eik_status mg_create(MgState **out, const Grid &g, const CellGrid &cg, int px, i
        cudaMalloc(&mg->p[0], 4 * np) == cudaSuccess && cudaMalloc(&mg->p[1], 4 * np) == cudaSuccess &&
        cudaMalloc(&mg->q, 4 * np) == cudaSuccess &&
        cudaMalloc(&mg->ctl, sizeof(MgCtl)) == cudaSuccess &&
-       cudaMalloc(&mg->part, 2 * sizeof(double) * mg->nblk) == cudaSuccess &&
+       cudaMalloc(&mg->part, 2 * sizeof(double) * mg->cap) == cudaSuccess &&
        cudaMallocHost(&mg->h_ctl, sizeof(MgCtl)) == cudaSuccess;
   if (ok) {
     // padding columns of the pitched arrays are read by no kernel; keep them finite
@@ -600,6 +689,14 @@ static int blocks_for(const MgState *mg, int64_t n) {
   return (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, mg->cap));
 }
 
+// Row-strided launch grid of a level: columns by blockIdx.x, rows by
+// blockIdx.y, at most cap blocks.
+static dim3 grid2(const MgState *mg, int nx, int ny) {
+  const int gx = std::max(1, std::min((nx + kThreads - 1) / kThreads, mg->cap));
+  const int gy = std::max(1, std::min(ny, mg->cap / gx));
+  return dim3((unsigned)gx, (unsigned)gy, 1);
+}
+
 eik_status mg_setup(MgState *mg, const MgFine &f, int kmin, cudaStream_t s) {
   const Grid &g = mg->g;
   k_mg_weights<<<mg->nblk, kThreads, 0, s>>>(g, mg->cg, mg->px, f.s32, f.kx, f.St, mg->w);
@@ -618,27 +715,42 @@ eik_status mg_setup(MgState *mg, const MgFine &f, int kmin, cudaStream_t s) {
 }
 
 // One PCG iteration (direction buffers: read p[set], write p[1 - set]).
+// First level handled by the tail kernel: the first of at most kTailNodes
+// nodes, level 1 at the earliest.
+static int tail_start(const MgState *mg) {
+  int l = 1;
+  while (l < (int)mg->lv.size() - 1 && (int64_t)mg->lv[l].nx * mg->lv[l].ny > kTailNodes) ++l;
+  return l;
+}
+
 static void launch_iter(MgState *mg, const MgFine &f, int set, cudaStream_t s) {
   const Grid &g = mg->g;
   const int L = (int)mg->lv.size() - 1;   // coarsest level index
-  k_mg_down0<<<blocks_for(mg, (int64_t)mg->lv[1].nx * mg->lv[1].ny), kThreads, 0, s>>>(
+  const dim3 g0 = grid2(mg, g.nx, g.ny);
+  k_mg_down0<<<grid2(mg, mg->lv[1].nx, mg->lv[1].ny), kThreads, 0, s>>>(
       g, mg->cg, mg->px, f.s32, f.kx, mg->w, f.r, mg->lv[1], mg->ctl);
-  for (int l = 1; l < L; ++l)
-    k_mg_down<<<blocks_for(mg, (int64_t)mg->lv[l + 1].nx * mg->lv[l + 1].ny), kThreads, 0, s>>>(
+  // levels 1 .. ts - 1 one launch each way; ts .. L in the single-block tail
+  const int ts = tail_start(mg);
+  for (int l = 1; l < ts; ++l)
+    k_mg_down<<<grid2(mg, mg->lv[l + 1].nx, mg->lv[l + 1].ny), kThreads, 0, s>>>(
         mg->lv[l], mg->lv[l + 1], mg->ctl);
-  k_mg_bottom<<<1, kThreads, 0, s>>>(mg->lv[L], mg->ctl);
-  for (int l = L - 1; l >= 1; --l)
-    k_mg_up<<<blocks_for(mg, (int64_t)mg->lv[l].nx * mg->lv[l].ny), kThreads, 0, s>>>(
-        mg->lv[l], mg->lv[l + 1], mg->ctl);
-  k_mg_up0<<<mg->nblk, kThreads, 0, s>>>(g, mg->cg, mg->px, f.s32, f.kx, mg->w, f.r, mg->lv[1],
-                                         mg->z, mg->ctl, mg->part);
-  k_mg_dir<<<mg->nblk, kThreads, 0, s>>>(g, mg->cg, mg->px, f.s32, f.kx, mg->z, mg->p[set],
-                                         mg->p[1 - set], mg->q, mg->ctl, mg->part);
-  k_mg_step<<<mg->nblk, kThreads, 0, s>>>(g, mg->px, mg->p[1 - set], mg->q, f.xref, f.d, f.r,
-                                          mg->ctl, mg->part, mg->nblk);
+  MgTail T{};
+  for (int l = ts; l <= L; ++l) T.lv[l] = mg->lv[l];
+  T.s = ts;
+  T.L = L;
+  k_mg_tail<<<1, kTailThreads, 0, s>>>(T, mg->ctl);
+  for (int l = ts - 1; l >= 1; --l)
+    k_mg_up<<<grid2(mg, mg->lv[l].nx, mg->lv[l].ny), kThreads, 0, s>>>(mg->lv[l], mg->lv[l + 1],
+                                                                         mg->ctl);
+  k_mg_up0<<<g0, kThreads, 0, s>>>(g, mg->cg, mg->px, f.s32, f.kx, mg->w, f.r, mg->lv[1], mg->z,
+                                   mg->ctl, mg->part);
+  k_mg_dir<<<g0, kThreads, 0, s>>>(g, mg->cg, mg->px, f.s32, f.kx, mg->z, mg->p[set],
+                                   mg->p[1 - set], mg->q, mg->ctl, mg->part);
+  k_mg_step<<<g0, kThreads, 0, s>>>(g, mg->px, mg->p[1 - set], mg->q, f.xref, f.d, f.r, mg->ctl,
+                                    mg->part, mg->cap);
 }
 
-static int launches_per_iter(const MgState *mg) { return 2 * ((int)mg->lv.size() - 1) + 3; }
+static int launches_per_iter(const MgState *mg) { return 2 * (tail_start(mg) - 1) + 5; }
 
 eik_status mg_inner(MgState *mg, const MgFine &f, MixCtl *h_st, cudaStream_t s) {
   if (mg->graph && (f.r != mg->bound.r || f.d != mg->bound.d || f.xref != mg->bound.xref ||
@@ -664,11 +776,25 @@ eik_status mg_inner(MgState *mg, const MgFine &f, MixCtl *h_st, cudaStream_t s) 
   c.first = 1;
   *mg->h_ctl = c;
   GCK(cudaMemcpyAsync(mg->ctl, mg->h_ctl, sizeof(MgCtl), cudaMemcpyHostToDevice, s));
+  if (mg->profile && !mg->ev[0])
+    for (auto &e : mg->ev) GCK(cudaEventCreate(&e));
+  int before = 0;
   for (;;) {
+    if (mg->profile) GCK(cudaEventRecord(mg->ev[0], s));
     GCK(cudaGraphLaunch(mg->graph, s));
-    mg->launches += kGraphIters * launches_per_iter(mg);
+    if (mg->profile) GCK(cudaEventRecord(mg->ev[1], s));
     GCK(cudaMemcpyAsync(mg->h_ctl, mg->ctl, sizeof(MgCtl), cudaMemcpyDeviceToHost, s));
     GCK(cudaStreamSynchronize(s));
+    // every kernel of the graph launches (those past the end return at once)
+    mg->launches += (int64_t)kGraphIters * launches_per_iter(mg);
+    const int done_iters = mg->h_ctl->iter - before;
+    before = mg->h_ctl->iter;
+    if (mg->profile && done_iters == kGraphIters) {
+      float t = 0.f;
+      GCK(cudaEventElapsedTime(&t, mg->ev[0], mg->ev[1]));
+      mg->ms += t;
+      mg->timed_iters += done_iters;
+    }
     if (mg->h_ctl->done) break;
   }
   h_st->iter = mg->h_ctl->iter;

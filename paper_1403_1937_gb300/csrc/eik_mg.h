@@ -30,6 +30,11 @@ eik_status mg_inner(MgState *mg, const MgFine &f, MixCtl *h_st, cudaStream_t s);
 void mg_destroy(MgState *mg);
 int mg_levels(const MgState *mg);
 int64_t mg_launches(const MgState *mg);
+// Profiling: CUDA events around every graph launch; mg_time returns the
+// iterations so timed and their device milliseconds.
+void mg_set_profiling(MgState *mg, bool on);
+void mg_time(const MgState *mg, int64_t *iters, double *ms);
+void mg_reset(MgState *mg);
 const char *mg_last_error();
 
 }  // namespace eik

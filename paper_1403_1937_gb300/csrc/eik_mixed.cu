@@ -495,6 +495,7 @@ int64_t mixed_kernel_launches(const MixedState *m, int k) {
 
 void mixed_reset_launches(MixedState *m) {
   if (!m) return;
+  mg_reset(m->mg);
   for (int k = 0; k < 8; ++k) {
     m->launches[k] = 0;
     m->timed[k] = 0;
@@ -504,9 +505,14 @@ void mixed_reset_launches(MixedState *m) {
 
 void mixed_set_profiling(MixedState *m, bool on) {
   if (m) m->profile = on;
+  if (m) mg_set_profiling(m->mg, on);
 }
 
 void mixed_kernel_time(const MixedState *m, int k, int64_t *timed, double *ms) {
+  if (m && k == 7) {   // one multigrid-preconditioned iteration (all its kernels)
+    mg_time(m->mg, timed, ms);
+    return;
+  }
   *timed = (m && k >= 0 && k < 8) ? m->timed[k] : 0;
   *ms = (m && k >= 0 && k < 8) ? m->ms[k] : 0.0;
 }
