@@ -54,9 +54,18 @@ ALGO_BYTES_PER_NODE = {
     # z) 17 B, direction (read z, p, sig; write p, q) 20 B, step (read p, q,
     # d, r; write d, r) 24 B; the coarse levels (read g, a, 4 coefficients,
     # k; write the next residual / read them again plus the parent
-    # correction, write y: ~62 B per coarse node, n/3 coarse nodes) ~21 B
+    # correction, write y: ~62 B per coarse node, n/3 coarse nodes) ~21 B;
+    # in 3D (six coefficients, n/7 coarse nodes of ~85 B, level-0 transfers
+    # of 1/8 per node) 73 + 12 = 85 B, see algo_bytes
     "mixed_mg": 95,
 }
+
+
+def algo_bytes(kernel, inst):
+    """Algorithmic bytes per node of one launch of ``kernel`` on ``inst``."""
+    if kernel == "mixed_mg" and len(inst.dims) == 3:
+        return 85
+    return ALGO_BYTES_PER_NODE[kernel]
 
 # The FP64 passes are bound by the FP64 pipe, not by HBM: their roofline is
 # algorithmic FP64 operations (an FMA counts 2) per node against the GB300's
@@ -330,7 +339,7 @@ def measure(args, wname, ws, local, modes=None):
         modes = [args.precision]
         if args.modes == "both":
             modes += [m for m in ("fp64", "mixed") if m != args.precision]
-        if len(inst.dims) == 2 and not args.no_mg:
+        if not args.no_mg:
             modes.append("mixed_mg")
     results = {}
     S_dev = torch.empty(inst.dims[::-1], dtype=torch.float64, device="cuda")
@@ -409,7 +418,7 @@ def kernel_table(res, inst):
             continue
         e = {"avg_us": round(avg_ms * 1e3, 2), "timed_launches": n}
         if k in ALGO_BYTES_PER_NODE:
-            gbs = ALGO_BYTES_PER_NODE[k] * inst.n / (avg_ms * 1e-3) / 1e9
+            gbs = algo_bytes(k, inst) * inst.n / (avg_ms * 1e-3) / 1e9
             e["achieved_gbs"] = round(gbs, 1)
             e["frac_of_hbm"] = round(gbs / peak, 4)
         out[k] = e
@@ -422,7 +431,8 @@ def secondary_block(args, ws, local):
     kernels (no CPU baseline, no e2e)."""
     saved = args.no_e2e
     args.no_e2e = True
-    inst, desc, n_unk, res = measure(args, "c3", ws, local, modes=["mixed", "fp64"])
+    modes = ["mixed", "fp64"] + ([] if args.no_mg else ["mixed_mg"])
+    inst, desc, n_unk, res = measure(args, "c3", ws, local, modes=modes)
     args.no_e2e = saved
     out = {"workload": desc["workload"]}
     for mode, r in res.items():
@@ -438,6 +448,14 @@ def secondary_block(args, ws, local):
             res["fp64"]["ms_per_step"] / res["mixed"]["ms_per_step"], 3)
         out["roofline"] = roofline(res["mixed"], inst, "c3")
         out["clocks"] = res["mixed"]["clocks"]
+    if "glups" in res.get("mixed_mg", {}):
+        out["mixed_mg"]["tol_componentwise"] = args.mg_tol
+        out["mixed_mg"]["roofline_iteration"] = roofline(res["mixed_mg"], inst, "c3",
+                                                         only="mixed_mg")
+        for ref in ("fp64", "mixed"):
+            if "glups" in res.get(ref, {}):
+                out[f"mixed_mg_speedup_vs_{ref}"] = round(
+                    res[ref]["ms_per_step"] / res["mixed_mg"]["ms_per_step"], 3)
     return out
 
 
@@ -830,7 +848,7 @@ def roofline(res, inst, wname, only=None):
                 "algorithmic_bytes_per_launch": ALGO_BYTES_PER_NODE[dom] * inst.n,
                 "avg_launch_ms": avg_ms,
                 "share_of_kernel_time": round(cand[dom][2] / total, 3) if total else None}
-    algo = ALGO_BYTES_PER_NODE[dom] * inst.n
+    algo = algo_bytes(dom, inst) * inst.n
     achieved = algo / (avg_ms * 1e-3) / 1e9
     return {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
             "peak": peak, "peak_source": peak_src, "unit": "GB/s",

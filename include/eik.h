@@ -73,12 +73,12 @@ enum {
 
 enum {
   EIK_PRECOND_JACOBI = 0,     /* Jacobi-PCG, one fused pass per iteration */
-  EIK_PRECOND_MULTIGRID = 1   /* 2D: PCG with a V-cycle of relative-form
+  EIK_PRECOND_MULTIGRID = 1   /* PCG with a V-cycle of relative-form
                                  aggregation multigrid (Sec. 6 names
                                  multigrid as the O(N) route for the sparse
                                  system): coarse basis functions are the
                                  estimated phi = exp(-S/hbar) on 2 x 2
-                                 boxes, so coarse corrections are relative
+                                 (x 2) boxes, so coarse corrections are relative
                                  ones and the far field converges with the
                                  near field */
 };
@@ -140,12 +140,12 @@ typedef struct {
                          fixes the pass's 2D variant; 0 = autotuned. */
   int precond;        /* EIK_PRECOND_*: preconditioner of the FP32 inner
                          solve in mixed mode; default EIK_PRECOND_JACOBI.
-                         EIK_PRECOND_MULTIGRID needs EIK_PREC_MIXED and a 2D
-                         grid (else EIK_ERR_ARG); its solves sweep level-set
+                         EIK_PRECOND_MULTIGRID needs EIK_PREC_MIXED (else
+                         EIK_ERR_ARG); its solves sweep level-set
                          bands only when phi spans more than 256 powers of
                          two (bands of 128; band_bits overrides both as for
                          Jacobi), and a batch of such instances solves per
-                         instance (batch_pack is ignored). */
+                         instance (batch_pack is ignored).  2D and 3D. */
   int reserved[2];
 } eik_options;
 

@@ -434,8 +434,8 @@ static eik_status create_impl(eik_handle **out, int ndim, const int64_t *dims, d
     return fail(EIK_ERR_ARG, "batch_tile_rows must be in 0..1024");
   if (o.precond != EIK_PRECOND_JACOBI && o.precond != EIK_PRECOND_MULTIGRID)
     return fail(EIK_ERR_ARG, "unknown precond");
-  if (o.precond == EIK_PRECOND_MULTIGRID && (o.precision != EIK_PREC_MIXED || ndim != 2))
-    return fail(EIK_ERR_ARG, "the multigrid preconditioner needs mixed precision and a 2D grid");
+  if (o.precond == EIK_PRECOND_MULTIGRID && o.precision != EIK_PREC_MIXED)
+    return fail(EIK_ERR_ARG, "the multigrid preconditioner needs mixed precision");
 
   eik_handle *h = new (std::nothrow) eik_handle();
   if (!h) return fail(EIK_ERR_OOM, "host allocation failed");

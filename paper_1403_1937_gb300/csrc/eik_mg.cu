@@ -1,4 +1,4 @@
-// Multigrid-preconditioned inner solve of the mixed-precision path (2D).
+// Multigrid-preconditioned inner solve of the mixed-precision path (2D, 3D).
 //
 // The paper names multigrid as the O(N) route for the sparse system of
 // Sec. 6 (Eq. sparse-system); this file builds one that keeps the relative
@@ -9,10 +9,10 @@
 // * Level 0 is the Jacobi-scaled operator of the correction equation in kx
 //   units, (A v)_i = v_i - sig_i sum_j omega_ij sig_j 2^(kx_i - kx_j) v_j,
 //   exactly as in the Jacobi-preconditioned inner CG.
-// * Coarse node C of level l + 1 aggregates a 2 x 2 box of level-l nodes.
-//   Its basis function is, on level 0, the estimated solution shape
+// * Coarse node C of level l + 1 aggregates a 2 x 2 (x 2) box of level-l
+//   nodes.  Its basis function is, on level 0, the estimated solution shape
 //   w_i = exp(kx_i ln 2 - St_i / hbar) / sig_i on the box (St_i: the cell
-//   distance estimate interpolated bilinearly between cell centres), so a
+//   distance estimate interpolated (bi/tri)linearly between cell centres), so a
 //   coarse unknown is a relative correction, constant on its box, of the
 //   estimated phi.  Coarser levels take unit weights, so every coarse basis
 //   function keeps that level-0 shape.
@@ -20,7 +20,7 @@
 //   symmetric) for vectors stored as value * 2^k, k a power-of-two exponent
 //   per node: (A y)_C = a_C y_C + sum_D c_CD y_D with the row-relative
 //   coefficients c_CD = A_CD 2^(k_C - k_D), one per neighbour (west, east,
-//   south, north), formed in FP64.  Between an aggregate and its upstream
+//   south, north, below, above), formed in FP64.  Between an aggregate and its upstream
 //   neighbour (nearer the sources) c is O(1); downstream it is tiny or 0.
 //   (Storing A_CD and the factor separately would overflow FP32 on coarse
 //   levels, where neighbouring exponents differ by over a hundred.)  The
@@ -35,8 +35,9 @@
 //   node solved exactly.  Sources (sig = 0) take no part in any transfer.
 //
 // The outer iteration is preconditioned CG on level 0 in kx units with the
-// true inner product, <u, v> = sum u_i v_i 2^(-2 kx_i) (FP64 sums, weights
-// relative to the smallest exponent; a weight below the FP64 range is 0),
+// true inner product, <u, v> = sum u_i v_i 2^(-2 kx_i) (per-thread FP32
+// sums, weights relative to the smallest exponent, 0 past the FP32 range;
+// FP64 across threads and blocks in a fixed order),
 // one graph launch per two iterations:
 //   z = M r, rho = <r, z>, beta = rho / rho_old, p = z + beta p, q = A p,
 //   alpha = rho / <p, q>, d += alpha p, r -= alpha q,
@@ -67,15 +68,16 @@ constexpr int kGraphIters = 2;          // even: the direction buffers alternate
 constexpr int kMaxInnerIters = 1000;
 thread_local std::string g_msg = "no error";
 
+enum { kW = 0, kE = 1, kS = 2, kN = 3, kB = 4, kT = 5, kDirs = 6 };
+
 struct MgLevel {
-  int nx = 0, ny = 0;
+  int nx = 0, ny = 0, nz = 1;
   float *a = nullptr;            // diagonal; a < 0 marks a node with no unknowns
   float *ia = nullptr;           // 1 / a (0 on nodes with no unknowns)
-  float *c = nullptr;            // 4 x nx*ny row-relative coefficients: W, E, S, N
+  float *c = nullptr;            // kDirs x m row-relative coefficients (W, E, S, N, B, T)
   int *k = nullptr;
   float *g = nullptr, *y = nullptr;
 };
-enum { kW = 0, kE = 1, kS = 2, kN = 3 };
 
 struct MgCtl {
   double rho;        // <r, z> of the current residual
@@ -85,12 +87,17 @@ struct MgCtl {
   unsigned int counter[4];
 };
 
-__device__ __forceinline__ int kx_at(const CellGrid &cg, int x, int y, const int *kx) {
-  return kx[(x >> cg.lgB) + cg.cx * (y >> cg.lgB)];
+__device__ __forceinline__ int kx_at(const CellGrid &cg, int x, int y, int z, const int *kx) {
+  return kx[(x >> cg.lgB) + cg.cx * ((y >> cg.lgB) + cg.cy * (z >> cg.lgB))];
 }
 __device__ __forceinline__ float face(int i, int n, int boundary) {
   return (boundary == EIK_BOUNDARY_HALF_CELL && (i == 0 || i == n - 1)) ? 0.5f : 1.f;
 }
+// the face factor of the z axis (1 in 2D, which has no z faces)
+__device__ __forceinline__ float facez(const Grid &g, int z) {
+  return (g.nz > 1) ? face(z, g.nz, g.boundary) : 1.f;
+}
+
 // 2^e from its bit pattern; 0 below the normal range (such factors only
 // scale terms that are negligible), e capped at 127.
 __device__ __forceinline__ float p2f(int e) {
@@ -98,90 +105,110 @@ __device__ __forceinline__ float p2f(int e) {
   return (e < -126) ? 0.f : __int_as_float((e + 127) << 23);
 }
 
-// Grid-stride loops over the rows (blockIdx.y) and columns (x) of a level:
-// no 64-bit division per node.
-#define MG_ROWS(ny_) for (int y = blockIdx.y; y < (ny_); y += gridDim.y)
+// Grid-stride loops over the rows (y, z) of a level (blockIdx.y) and its
+// columns x: no 64-bit division per node.
+#define MG_ROWS(ny_, nz_)                                              \
+  for (int rr = blockIdx.y; rr < (ny_) * (nz_); rr += gridDim.y)      \
+    for (int y = rr % (ny_), z = rr / (ny_), once_ = 1; once_; once_ = 0)
 #define MG_COLS(nx_) \
   for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < (nx_); x += gridDim.x * blockDim.x)
 
 // Level-0 off-diagonal sum  sig_i sum_j omega_ij sig_j 2^(k_i - k_j) v(j)
-// for the node (x, y); v(j, xj, yj) gives the vector at pitched index j.
-// The exponent is looked up only where the neighbour lies in another cell.
+// for the node (x, y, z); v(j, xj, yj, zj) gives the vector at pitched
+// index j.  The exponent is looked up only where the neighbour lies in
+// another cell.  Edge weights: the product of the face factors of the other
+// axes (Sec. 6 with zero-flux faces, half cells on the faces).
 template <class V>
 __device__ __forceinline__ float nb0(const Grid &g, const CellGrid &cg, int px,
                                      const float *__restrict__ s32, const int *__restrict__ kx,
-                                     int x, int y, int ki, V v) {
+                                     int x, int y, int z, int ki, V v) {
   float acc = 0.f;
   const int mask = cg.B - 1;
-  const float hy = face(y, g.ny, g.boundary), hx = face(x, g.nx, g.boundary);
-  const int64_t i = (int64_t)y * px + x;
+  const float hx = face(x, g.nx, g.boundary), hy = face(y, g.ny, g.boundary), hz = facez(g, z);
+  const int64_t pz = (int64_t)px * g.ny;
+  const int64_t i = x + (int64_t)px * (y + (int64_t)g.ny * z);
   if (x > 0) {
-    const float f = ((x & mask) == 0) ? p2f(ki - kx_at(cg, x - 1, y, kx)) : 1.f;
-    acc = fmaf(hy * s32[i - 1] * f, v(i - 1, x - 1, y), acc);
+    const float f = ((x & mask) == 0) ? p2f(ki - kx_at(cg, x - 1, y, z, kx)) : 1.f;
+    acc = fmaf(hy * hz * s32[i - 1] * f, v(i - 1, x - 1, y, z), acc);
   }
   if (x + 1 < g.nx) {
-    const float f = (((x + 1) & mask) == 0) ? p2f(ki - kx_at(cg, x + 1, y, kx)) : 1.f;
-    acc = fmaf(hy * s32[i + 1] * f, v(i + 1, x + 1, y), acc);
+    const float f = (((x + 1) & mask) == 0) ? p2f(ki - kx_at(cg, x + 1, y, z, kx)) : 1.f;
+    acc = fmaf(hy * hz * s32[i + 1] * f, v(i + 1, x + 1, y, z), acc);
   }
   if (y > 0) {
-    const float f = ((y & mask) == 0) ? p2f(ki - kx_at(cg, x, y - 1, kx)) : 1.f;
-    acc = fmaf(hx * s32[i - px] * f, v(i - px, x, y - 1), acc);
+    const float f = ((y & mask) == 0) ? p2f(ki - kx_at(cg, x, y - 1, z, kx)) : 1.f;
+    acc = fmaf(hx * hz * s32[i - px] * f, v(i - px, x, y - 1, z), acc);
   }
   if (y + 1 < g.ny) {
-    const float f = (((y + 1) & mask) == 0) ? p2f(ki - kx_at(cg, x, y + 1, kx)) : 1.f;
-    acc = fmaf(hx * s32[i + px] * f, v(i + px, x, y + 1), acc);
+    const float f = (((y + 1) & mask) == 0) ? p2f(ki - kx_at(cg, x, y + 1, z, kx)) : 1.f;
+    acc = fmaf(hx * hz * s32[i + px] * f, v(i + px, x, y + 1, z), acc);
+  }
+  if (z > 0) {
+    const float f = ((z & mask) == 0) ? p2f(ki - kx_at(cg, x, y, z - 1, kx)) : 1.f;
+    acc = fmaf(hx * hy * s32[i - pz] * f, v(i - pz, x, y, z - 1), acc);
+  }
+  if (z + 1 < g.nz) {
+    const float f = (((z + 1) & mask) == 0) ? p2f(ki - kx_at(cg, x, y, z + 1, kx)) : 1.f;
+    acc = fmaf(hx * hy * s32[i + pz] * f, v(i + pz, x, y, z + 1), acc);
   }
   return s32[i] * acc;
 }
 
-// Coarse-level operator (A u)_C for node (x, y) of a level, u by functor of
-// the dense index.
+// Coarse-level operator (A u)_t for node (x, y, z) of a level; u(j, xj, yj,
+// zj) by dense index and coordinates.
 template <class V>
-__device__ __forceinline__ float apply_l(const MgLevel &L, int x, int y, V u) {
-  const int64_t i = (int64_t)y * L.nx + x;
-  const int64_t m = (int64_t)L.nx * L.ny;
-  float acc = fabsf(L.a[i]) * u(i);
-  if (x > 0) acc = fmaf(L.c[kW * m + i], u(i - 1), acc);
-  if (x + 1 < L.nx) acc = fmaf(L.c[kE * m + i], u(i + 1), acc);
-  if (y > 0) acc = fmaf(L.c[kS * m + i], u(i - L.nx), acc);
-  if (y + 1 < L.ny) acc = fmaf(L.c[kN * m + i], u(i + L.nx), acc);
+__device__ __forceinline__ float apply_l(const MgLevel &L, int x, int y, int z, V u) {
+  const int64_t m = (int64_t)L.nx * L.ny * L.nz;
+  const int64_t pl = (int64_t)L.nx * L.ny;
+  const int64_t i = x + (int64_t)L.nx * (y + (int64_t)L.ny * z);
+  float acc = fabsf(L.a[i]) * u(i, x, y, z);
+  if (x > 0) acc = fmaf(L.c[kW * m + i], u(i - 1, x - 1, y, z), acc);
+  if (x + 1 < L.nx) acc = fmaf(L.c[kE * m + i], u(i + 1, x + 1, y, z), acc);
+  if (y > 0) acc = fmaf(L.c[kS * m + i], u(i - L.nx, x, y - 1, z), acc);
+  if (y + 1 < L.ny) acc = fmaf(L.c[kN * m + i], u(i + L.nx, x, y + 1, z), acc);
+  if (z > 0) acc = fmaf(L.c[kB * m + i], u(i - pl, x, y, z - 1), acc);
+  if (z + 1 < L.nz) acc = fmaf(L.c[kT * m + i], u(i + pl, x, y, z + 1), acc);
   return acc;
 }
 
 // ------------------------------------------------------------- setup
 // w_i = exp(kx_i ln 2 - St_i / hbar) / sig_i (0 on the sources); St_i
-// bilinear between the cell centres (flat beyond the outer ones).
+// interpolated linearly along each axis between the cell centres (flat
+// beyond the outer ones).
 __global__ void k_mg_weights(Grid g, CellGrid cg, int px, const float *__restrict__ s32,
                              const int *__restrict__ kx, const float *__restrict__ St,
                              float *__restrict__ w) {
-  const int64_t n = (int64_t)g.nx * g.ny;
   const float B = (float)cg.B, half = 0.5f * (B - 1.f);
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(t % g.nx), y = (int)(t / g.nx);
-    const int64_t i = (int64_t)y * px + x;
+  auto axis = [&](int c, int ncell, int nn, int &I0, int &I1, float &tt) {
+    I0 = min(max((int)floorf(((float)c - half) / B), 0), ncell - 1);
+    I1 = min(I0 + 1, ncell - 1);
+    const float c0 = fminf(I0 * B + half, (float)(nn - 1));
+    const float c1 = fminf(I1 * B + half, (float)(nn - 1));
+    tt = (c1 > c0) ? fminf(fmaxf(((float)c - c0) / (c1 - c0), 0.f), 1.f) : 0.f;
+  };
+  MG_ROWS(g.ny, g.nz) MG_COLS(g.nx) {
+    const int64_t i = x + (int64_t)px * rr;
     const float s = s32[i];
     if (s == 0.f) {
       w[i] = 0.f;
       continue;
     }
-    auto axis = [&](int c, int ncell, int nn, int &I0, int &I1, float &tt) {
-      I0 = min(max((int)floorf(((float)c - half) / B), 0), ncell - 1);
-      I1 = min(I0 + 1, ncell - 1);
-      const float c0 = fminf(I0 * B + half, (float)(nn - 1));
-      const float c1 = fminf(I1 * B + half, (float)(nn - 1));
-      tt = (c1 > c0) ? fminf(fmaxf(((float)c - c0) / (c1 - c0), 0.f), 1.f) : 0.f;
-    };
-    int I0, I1, J0, J1;
-    float tx, ty;
+    int I0, I1, J0, J1, K0, K1;
+    float tx, ty, tz;
     axis(x, cg.cx, g.nx, I0, I1, tx);
     axis(y, cg.cy, g.ny, J0, J1, ty);
-    const float s00 = St[I0 + cg.cx * J0], s10 = St[I1 + cg.cx * J0];
-    const float s01 = St[I0 + cg.cx * J1], s11 = St[I1 + cg.cx * J1];
-    const int ki = kx_at(cg, x, y, kx);
+    axis(z, cg.cz, g.nz, K0, K1, tz);
+    auto Sc = [&](int I, int J, int K) { return St[I + cg.cx * (J + cg.cy * K)]; };
+    const float v[8] = {Sc(I0, J0, K0), Sc(I1, J0, K0), Sc(I0, J1, K0), Sc(I1, J1, K0),
+                        Sc(I0, J0, K1), Sc(I1, J0, K1), Sc(I0, J1, K1), Sc(I1, J1, K1)};
+    bool fin = true;
+    for (int q = 0; q < 8; ++q) fin = fin && isfinite(v[q]);
+    const int ki = kx_at(cg, x, y, z, kx);
     float ex = 0.f;
-    if (isfinite(s00) && isfinite(s10) && isfinite(s01) && isfinite(s11)) {
-      const float Sb = (1.f - ty) * ((1.f - tx) * s00 + tx * s10) + ty * ((1.f - tx) * s01 + tx * s11);
+    if (fin) {
+      const float b0 = (1.f - ty) * ((1.f - tx) * v[0] + tx * v[1]) + ty * ((1.f - tx) * v[2] + tx * v[3]);
+      const float b1 = (1.f - ty) * ((1.f - tx) * v[4] + tx * v[5]) + ty * ((1.f - tx) * v[6] + tx * v[7]);
+      const float Sb = (1.f - tz) * b0 + tz * b1;
       ex = (float)((double)ki * 0.69314718055994530942 - (double)Sb / g.hbar);
       ex = fminf(fmaxf(ex, -30.f), 30.f);   // w^2 stays in the FP32 range
     }
@@ -189,119 +216,135 @@ __global__ void k_mg_weights(Grid g, CellGrid cg, int px, const float *__restric
   }
 }
 
-// Level 1 from level 0: P_i = w_i (one exponent per 2 x 2 box: boxes lie
-// inside one cell), true A_ij = -sig_i sig_j omega_ij; c_CD = 2^(k_C - k_D)
-// sum w_i w_j A_ij over the edges between the two boxes.  Sums in FP64.
+// Level 1 from level 0: P_i = w_i (one exponent per box: boxes lie inside
+// one cell), true A_ij = -sig_i sig_j omega_ij; c_CD = 2^(k_C - k_D) sum
+// w_i w_j A_ij over the edges between the two boxes.  Sums in FP64.
 __global__ void k_mg_coarsen0(Grid g, CellGrid cg, int px, const float *__restrict__ s32,
                               const int *__restrict__ kx, const float *__restrict__ w, MgLevel L) {
-  const int64_t m = (int64_t)L.nx * L.ny;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int X = (int)(t % L.nx), Y = (int)(t / L.nx);
-    const int x0 = 2 * X, y0 = 2 * Y;
-    const int x1 = min(x0 + 1, g.nx - 1), y1 = min(y0 + 1, g.ny - 1);
-    auto W = [&](int x, int y) { return (double)w[(int64_t)y * px + x]; };
-    auto S = [&](int x, int y) { return (double)s32[(int64_t)y * px + x]; };
-    // A_ij of the x-edge (xa, y)-(xa + 1, y) and of the y-edge (x, ya)-(x, ya + 1)
-    auto ax = [&](int xa, int y) {
-      return -S(xa, y) * S(xa + 1, y) * (double)face(y, g.ny, g.boundary);
+  const int64_t m = (int64_t)L.nx * L.ny * L.nz;
+  MG_ROWS(L.ny, L.nz) MG_COLS(L.nx) {
+    const int64_t t = x + (int64_t)L.nx * rr;
+    const int x0 = 2 * x, y0 = 2 * y, z0 = 2 * z;
+    const int x1 = min(x0 + 1, g.nx - 1), y1 = min(y0 + 1, g.ny - 1), z1 = min(z0 + 1, g.nz - 1);
+    auto at = [&](int a, int b, int c) { return a + (int64_t)px * (b + (int64_t)g.ny * c); };
+    auto W = [&](int a, int b, int c) { return (double)w[at(a, b, c)]; };
+    auto S = [&](int a, int b, int c) { return (double)s32[at(a, b, c)]; };
+    // A_ij of the edges (a, b, c)-(a + 1, b, c), (a, b, c)-(a, b + 1, c), (a, b, c)-(a, b, c + 1)
+    auto ax = [&](int a, int b, int c) {
+      return -S(a, b, c) * S(a + 1, b, c) * (double)(face(b, g.ny, g.boundary) * facez(g, c));
     };
-    auto ay = [&](int x, int ya) {
-      return -S(x, ya) * S(x, ya + 1) * (double)face(x, g.nx, g.boundary);
+    auto ay = [&](int a, int b, int c) {
+      return -S(a, b, c) * S(a, b + 1, c) * (double)(face(a, g.nx, g.boundary) * facez(g, c));
     };
-    const int kc = kx_at(cg, x0, y0, kx);
-    double A = 0.0, cW = 0.0, cE = 0.0, cS = 0.0, cN = 0.0;
+    auto az = [&](int a, int b, int c) {
+      return -S(a, b, c) * S(a, b, c + 1) *
+             (double)(face(a, g.nx, g.boundary) * face(b, g.ny, g.boundary));
+    };
+    const int kc = kx_at(cg, x0, y0, z0, kx);
+    double A = 0.0, cd[kDirs] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     bool live = false;
-    for (int y = y0; y <= y1; ++y)
-      for (int x = x0; x <= x1; ++x) {
-        const double wi = W(x, y);
-        if (wi != 0.0) live = true;
-        A += wi * wi;
+    for (int c = z0; c <= z1; ++c)
+      for (int b = y0; b <= y1; ++b)
+        for (int a = x0; a <= x1; ++a) {
+          const double wi = W(a, b, c);
+          if (wi != 0.0) live = true;
+          A += wi * wi;
+        }
+    for (int c = z0; c <= z1; ++c)
+      for (int b = y0; b <= y1; ++b) {
+        if (x1 > x0) A += 2.0 * W(x0, b, c) * W(x1, b, c) * ax(x0, b, c);
+        if (x > 0) cd[kW] += W(x0, b, c) * W(x0 - 1, b, c) * ax(x0 - 1, b, c);
+        if (x + 1 < L.nx && x0 + 2 < g.nx) cd[kE] += W(x1, b, c) * W(x0 + 2, b, c) * ax(x1, b, c);
       }
-    if (x1 > x0)
-      for (int y = y0; y <= y1; ++y) A += 2.0 * W(x0, y) * W(x1, y) * ax(x0, y);
-    if (y1 > y0)
-      for (int x = x0; x <= x1; ++x) A += 2.0 * W(x, y0) * W(x, y1) * ay(x, y0);
-    if (X > 0) {
-      const double f = ldexp(1.0, kc - kx_at(cg, x0 - 2, y0, kx));
-      for (int y = y0; y <= y1; ++y) cW += W(x0, y) * W(x0 - 1, y) * ax(x0 - 1, y);
-      cW *= f;
-    }
-    if (X + 1 < L.nx && x0 + 2 < g.nx) {
-      const double f = ldexp(1.0, kc - kx_at(cg, x0 + 2, y0, kx));
-      for (int y = y0; y <= y1; ++y) cE += W(x1, y) * W(x0 + 2, y) * ax(x1, y);
-      cE *= f;
-    }
-    if (Y > 0) {
-      const double f = ldexp(1.0, kc - kx_at(cg, x0, y0 - 2, kx));
-      for (int x = x0; x <= x1; ++x) cS += W(x, y0) * W(x, y0 - 1) * ay(x, y0 - 1);
-      cS *= f;
-    }
-    if (Y + 1 < L.ny && y0 + 2 < g.ny) {
-      const double f = ldexp(1.0, kc - kx_at(cg, x0, y0 + 2, kx));
-      for (int x = x0; x <= x1; ++x) cN += W(x, y1) * W(x, y0 + 2) * ay(x, y1);
-      cN *= f;
-    }
+    for (int c = z0; c <= z1; ++c)
+      for (int a = x0; a <= x1; ++a) {
+        if (y1 > y0) A += 2.0 * W(a, y0, c) * W(a, y1, c) * ay(a, y0, c);
+        if (y > 0) cd[kS] += W(a, y0, c) * W(a, y0 - 1, c) * ay(a, y0 - 1, c);
+        if (y + 1 < L.ny && y0 + 2 < g.ny) cd[kN] += W(a, y1, c) * W(a, y0 + 2, c) * ay(a, y1, c);
+      }
+    for (int b = y0; b <= y1; ++b)
+      for (int a = x0; a <= x1; ++a) {
+        if (z1 > z0) A += 2.0 * W(a, b, z0) * W(a, b, z1) * az(a, b, z0);
+        if (z > 0) cd[kB] += W(a, b, z0) * W(a, b, z0 - 1) * az(a, b, z0 - 1);
+        if (z + 1 < L.nz && z0 + 2 < g.nz) cd[kT] += W(a, b, z1) * W(a, b, z0 + 2) * az(a, b, z1);
+      }
+    // row-relative: times 2^(k_C - k_D), k_D the neighbouring box's cell exponent
+    if (x > 0) cd[kW] *= ldexp(1.0, kc - kx_at(cg, x0 - 2, y0, z0, kx));
+    if (x + 1 < L.nx && x0 + 2 < g.nx) cd[kE] *= ldexp(1.0, kc - kx_at(cg, x0 + 2, y0, z0, kx));
+    if (y > 0) cd[kS] *= ldexp(1.0, kc - kx_at(cg, x0, y0 - 2, z0, kx));
+    if (y + 1 < L.ny && y0 + 2 < g.ny) cd[kN] *= ldexp(1.0, kc - kx_at(cg, x0, y0 + 2, z0, kx));
+    if (z > 0) cd[kB] *= ldexp(1.0, kc - kx_at(cg, x0, y0, z0 - 2, kx));
+    if (z + 1 < L.nz && z0 + 2 < g.nz) cd[kT] *= ldexp(1.0, kc - kx_at(cg, x0, y0, z0 + 2, kx));
     L.a[t] = live ? (float)A : -1.f;
     L.ia[t] = live ? (float)(1.0 / A) : 0.f;
-    L.c[kW * m + t] = live ? (float)cW : 0.f;
-    L.c[kE * m + t] = live ? (float)cE : 0.f;
-    L.c[kS * m + t] = live ? (float)cS : 0.f;
-    L.c[kN * m + t] = live ? (float)cN : 0.f;
+    for (int d = 0; d < kDirs; ++d) L.c[d * m + t] = live ? (float)cd[d] : 0.f;
     L.k[t] = kc;
   }
 }
 
-// Smallest exponent over the live nodes of the box (X, Y) of level F;
+// Smallest exponent over the live nodes of the box (X, Y, Z) of level F;
 // INT_MAX when it has none.
-__device__ __forceinline__ int box_k(const MgLevel &F, int X, int Y) {
+__device__ __forceinline__ int box_k(const MgLevel &F, int X, int Y, int Z) {
   int k = INT_MAX;
-  for (int y = 2 * Y; y <= min(2 * Y + 1, F.ny - 1); ++y)
-    for (int x = 2 * X; x <= min(2 * X + 1, F.nx - 1); ++x) {
-      const int64_t i = (int64_t)y * F.nx + x;
-      if (F.a[i] >= 0.f) k = min(k, F.k[i]);
-    }
+  for (int z = 2 * Z; z <= min(2 * Z + 1, F.nz - 1); ++z)
+    for (int y = 2 * Y; y <= min(2 * Y + 1, F.ny - 1); ++y)
+      for (int x = 2 * X; x <= min(2 * X + 1, F.nx - 1); ++x) {
+        const int64_t i = x + (int64_t)F.nx * (y + (int64_t)F.ny * z);
+        if (F.a[i] >= 0.f) k = min(k, F.k[i]);
+      }
   return k;
 }
 
 // Level l + 1 (C) from level l (F): rows restricted with 2^(2(k_C - k_i)),
 // columns prolonged with unit weight (live nodes only).
 __global__ void k_mg_coarsen(MgLevel F, MgLevel C) {
-  const int64_t m = (int64_t)C.nx * C.ny;
-  const int64_t mf = (int64_t)F.nx * F.ny;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int X = (int)(t % C.nx), Y = (int)(t / C.nx);
-    const int kc = box_k(F, X, Y);
+  const int64_t m = (int64_t)C.nx * C.ny * C.nz;
+  const int64_t mf = (int64_t)F.nx * F.ny * F.nz;
+  const int64_t plf = (int64_t)F.nx * F.ny;
+  MG_ROWS(C.ny, C.nz) MG_COLS(C.nx) {
+    const int64_t t = x + (int64_t)C.nx * rr;
+    const int kc = box_k(F, x, y, z);
     if (kc == INT_MAX) {
       C.a[t] = -1.f;
       C.ia[t] = 0.f;
-      for (int d = 0; d < 4; ++d) C.c[d * m + t] = 0.f;
-      C.k[t] = F.k[(int64_t)(2 * Y) * F.nx + 2 * X];
+      for (int d = 0; d < kDirs; ++d) C.c[d * m + t] = 0.f;
+      C.k[t] = F.k[2 * x + (int64_t)F.nx * (2 * y + (int64_t)F.ny * 2 * z)];
       continue;
     }
-    const int x0 = 2 * X, y0 = 2 * Y;
-    const int x1 = min(x0 + 1, F.nx - 1), y1 = min(y0 + 1, F.ny - 1);
-    double A = 0.0, cW = 0.0, cE = 0.0, cS = 0.0, cN = 0.0;
-    for (int y = y0; y <= y1; ++y)
-      for (int x = x0; x <= x1; ++x) {
-        const int64_t i = (int64_t)y * F.nx + x;
-        if (F.a[i] < 0.f) continue;
-        const double r = ldexp(1.0, 2 * (kc - F.k[i]));
-        double row = (double)F.a[i];
-        // neighbours inside the box join the diagonal, the others the links
-        if (x > 0) (x - 1 >= x0 ? row : cW) += (x - 1 >= x0 ? 1.0 : r) * (double)F.c[kW * mf + i];
-        if (x + 1 < F.nx) (x + 1 <= x1 ? row : cE) += (x + 1 <= x1 ? 1.0 : r) * (double)F.c[kE * mf + i];
-        if (y > 0) (y - 1 >= y0 ? row : cS) += (y - 1 >= y0 ? 1.0 : r) * (double)F.c[kS * mf + i];
-        if (y + 1 < F.ny) (y + 1 <= y1 ? row : cN) += (y + 1 <= y1 ? 1.0 : r) * (double)F.c[kN * mf + i];
-        A += r * row;
-      }
+    const int x0 = 2 * x, y0 = 2 * y, z0 = 2 * z;
+    const int x1 = min(x0 + 1, F.nx - 1), y1 = min(y0 + 1, F.ny - 1), z1 = min(z0 + 1, F.nz - 1);
+    double A = 0.0, cd[kDirs] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int c = z0; c <= z1; ++c)
+      for (int b = y0; b <= y1; ++b)
+        for (int a = x0; a <= x1; ++a) {
+          const int64_t i = a + (int64_t)F.nx * (b + (int64_t)F.ny * c);
+          if (F.a[i] < 0.f) continue;
+          const double r = ldexp(1.0, 2 * (kc - F.k[i]));
+          double row = (double)F.a[i];
+          // neighbours inside the box join the diagonal, the others the links
+          auto add = [&](bool exists, bool inside, int d) {
+            if (!exists) return;
+            const double cij = (double)F.c[d * mf + i];
+            if (inside) row += cij;
+            else cd[d] += r * cij;
+          };
+          add(a > 0, a - 1 >= x0, kW);
+          add(a + 1 < F.nx, a + 1 <= x1, kE);
+          add(b > 0, b - 1 >= y0, kS);
+          add(b + 1 < F.ny, b + 1 <= y1, kN);
+          add(c > 0, c - 1 >= z0, kB);
+          add(c + 1 < F.nz, c + 1 <= z1, kT);
+          A += r * row;
+        }
+    (void)plf;
     C.a[t] = (float)A;
     C.ia[t] = (float)(1.0 / A);
-    C.c[kW * m + t] = (X > 0) ? (float)cW : 0.f;
-    C.c[kE * m + t] = (X + 1 < C.nx) ? (float)cE : 0.f;
-    C.c[kS * m + t] = (Y > 0) ? (float)cS : 0.f;
-    C.c[kN * m + t] = (Y + 1 < C.ny) ? (float)cN : 0.f;
+    C.c[kW * m + t] = (x > 0) ? (float)cd[kW] : 0.f;
+    C.c[kE * m + t] = (x + 1 < C.nx) ? (float)cd[kE] : 0.f;
+    C.c[kS * m + t] = (y > 0) ? (float)cd[kS] : 0.f;
+    C.c[kN * m + t] = (y + 1 < C.ny) ? (float)cd[kN] : 0.f;
+    C.c[kB * m + t] = (z > 0) ? (float)cd[kB] : 0.f;
+    C.c[kT * m + t] = (z + 1 < C.nz) ? (float)cd[kT] : 0.f;
     C.k[t] = kc;
   }
 }
@@ -312,77 +355,71 @@ __global__ void k_mg_down0(Grid g, CellGrid cg, int px, const float *__restrict_
                            const int *__restrict__ kx, const float *__restrict__ w,
                            const float *__restrict__ r, MgLevel L1, const MgCtl *ctl) {
   if (ctl->done) return;
-  auto rv = [&](int64_t j, int, int) { return r[j]; };
-  MG_ROWS(L1.ny) MG_COLS(L1.nx) {
-    const int X = x, Y = y;
+  auto rv = [&](int64_t j, int, int, int) { return r[j]; };
+  MG_ROWS(L1.ny, L1.nz) MG_COLS(L1.nx) {
     float sum = 0.f;
-    for (int yy = 2 * Y; yy <= min(2 * Y + 1, g.ny - 1); ++yy)
-      for (int xx = 2 * X; xx <= min(2 * X + 1, g.nx - 1); ++xx) {
-        const int64_t i = (int64_t)yy * px + xx;
-        const float wi = w[i];
-        if (wi == 0.f) continue;
-        const int ki = kx_at(cg, xx, yy, kx);
-        const float off = nb0(g, cg, px, s32, kx, xx, yy, ki, rv);
-        // (A (omega r))_i = omega (r_i - off)
-        const float ti = r[i] - kOmega * (r[i] - off);
-        sum = fmaf(wi, ti, sum);
-      }
-    L1.g[(int64_t)Y * L1.nx + X] = sum;
+    for (int cz = 2 * z; cz <= min(2 * z + 1, g.nz - 1); ++cz)
+      for (int cy = 2 * y; cy <= min(2 * y + 1, g.ny - 1); ++cy)
+        for (int cx = 2 * x; cx <= min(2 * x + 1, g.nx - 1); ++cx) {
+          const int64_t i = cx + (int64_t)px * (cy + (int64_t)g.ny * cz);
+          const float wi = w[i];
+          if (wi == 0.f) continue;
+          const int ki = kx_at(cg, cx, cy, cz, kx);
+          const float off = nb0(g, cg, px, s32, kx, cx, cy, cz, ki, rv);
+          // (A (omega r))_i = omega (r_i - off)
+          const float ti = r[i] - kOmega * (r[i] - off);
+          sum = fmaf(wi, ti, sum);
+        }
+    L1.g[x + (int64_t)L1.nx * rr] = sum;
   }
 }
 
-// Level l down (l >= 1) at coarse node (x, y): y = omega g / a on the box,
-// t = g - A y, restricted to level l + 1.
-__device__ __forceinline__ void down_node(const MgLevel &F, const MgLevel &C, int x, int y) {
-  auto yv = [&](int64_t j) { return kOmega * F.g[j] * F.ia[j]; };
-  const int64_t t = (int64_t)y * C.nx + x;
+// Level l down (l >= 1) at coarse node (x, y, z): y = omega g / a on the
+// box, t = g - A y, restricted to level l + 1.
+__device__ __forceinline__ void down_node(const MgLevel &F, const MgLevel &C, int x, int y, int z) {
+  auto yv = [&](int64_t j, int, int, int) { return kOmega * F.g[j] * F.ia[j]; };
+  const int64_t t = x + (int64_t)C.nx * (y + (int64_t)C.ny * z);
   const int kc = C.k[t];
   float sum = 0.f;
   if (C.a[t] >= 0.f) {
-    for (int yy = 2 * y; yy <= min(2 * y + 1, F.ny - 1); ++yy)
-      for (int xx = 2 * x; xx <= min(2 * x + 1, F.nx - 1); ++xx) {
-        const int64_t i = (int64_t)yy * F.nx + xx;
-        if (F.a[i] < 0.f) continue;
-        const float ti = F.g[i] - apply_l(F, xx, yy, yv);
-        sum = fmaf(p2f(2 * (kc - F.k[i])), ti, sum);
-      }
+    for (int cz = 2 * z; cz <= min(2 * z + 1, F.nz - 1); ++cz)
+      for (int cy = 2 * y; cy <= min(2 * y + 1, F.ny - 1); ++cy)
+        for (int cx = 2 * x; cx <= min(2 * x + 1, F.nx - 1); ++cx) {
+          const int64_t i = cx + (int64_t)F.nx * (cy + (int64_t)F.ny * cz);
+          if (F.a[i] < 0.f) continue;
+          const float ti = F.g[i] - apply_l(F, cx, cy, cz, yv);
+          sum = fmaf(p2f(2 * (kc - F.k[i])), ti, sum);
+        }
   }
   C.g[t] = sum;
 }
 
 __global__ void k_mg_down(MgLevel F, MgLevel C, const MgCtl *ctl) {
   if (ctl->done) return;
-  MG_ROWS(C.ny) MG_COLS(C.nx) down_node(F, C, x, y);
+  MG_ROWS(C.ny, C.nz) MG_COLS(C.nx) down_node(F, C, x, y, z);
 }
 
-// Level l up (l >= 1) at node (x, y): u = omega g / a + y(parent);
+// Level l up (l >= 1) at node (x, y, z): u = omega g / a + y(parent);
 // y = u + omega (g - A u) / a.
-__device__ __forceinline__ void up_node(const MgLevel &F, const MgLevel &C, int x, int y) {
-  {
-    const int64_t t = (int64_t)y * F.nx + x;
-    if (F.a[t] < 0.f) {
-      F.y[t] = 0.f;
-      return;
-    }
-    // u at the node (xj, yj) = index j of this level
-    auto uat = [&](int64_t j, int xj, int yj) {
-      const float par = (F.a[j] >= 0.f) ? C.y[(int64_t)(yj >> 1) * C.nx + (xj >> 1)] : 0.f;
-      return fmaf(kOmega * F.g[j], F.ia[j], par);
-    };
-    const int64_t m = (int64_t)F.nx * F.ny;
-    const float ut = uat(t, x, y);
-    float Au = fabsf(F.a[t]) * ut;
-    if (x > 0) Au = fmaf(F.c[kW * m + t], uat(t - 1, x - 1, y), Au);
-    if (x + 1 < F.nx) Au = fmaf(F.c[kE * m + t], uat(t + 1, x + 1, y), Au);
-    if (y > 0) Au = fmaf(F.c[kS * m + t], uat(t - F.nx, x, y - 1), Au);
-    if (y + 1 < F.ny) Au = fmaf(F.c[kN * m + t], uat(t + F.nx, x, y + 1), Au);
-    F.y[t] = fmaf(kOmega * (F.g[t] - Au), F.ia[t], ut);
+__device__ __forceinline__ void up_node(const MgLevel &F, const MgLevel &C, int x, int y, int z) {
+  const int64_t t = x + (int64_t)F.nx * (y + (int64_t)F.ny * z);
+  if (F.a[t] < 0.f) {
+    F.y[t] = 0.f;
+    return;
   }
+  auto uat = [&](int64_t j, int xj, int yj, int zj) {
+    const float par =
+        (F.a[j] >= 0.f) ? C.y[(xj >> 1) + (int64_t)C.nx * ((yj >> 1) + (int64_t)C.ny * (zj >> 1))] : 0.f;
+    return fmaf(kOmega * F.g[j], F.ia[j], par);
+  };
+  const float ut = uat(t, x, y, z);
+  const float Au = apply_l(F, x, y, z, uat);
+  F.y[t] = fmaf(kOmega * (F.g[t] - Au), F.ia[t], ut);
 }
 
 __global__ void k_mg_up(MgLevel F, MgLevel C, const MgCtl *ctl) {
   if (ctl->done) return;
-  MG_ROWS(F.ny) MG_COLS(F.nx) up_node(F, C, x, y);
+  MG_ROWS(F.ny, F.nz) MG_COLS(F.nx) up_node(F, C, x, y, z);
 }
 
 // The small levels s .. L of the V-cycle in one block: down sweeps, the
@@ -398,18 +435,22 @@ __global__ void __launch_bounds__(kTailThreads) k_mg_tail(MgTail T, const MgCtl 
   if (ctl->done) return;
   for (int l = T.s; l < T.L; ++l) {
     const MgLevel &F = T.lv[l], &C = T.lv[l + 1];
-    for (int t = threadIdx.x; t < C.nx * C.ny; t += blockDim.x) down_node(F, C, t % C.nx, t / C.nx);
+    const int m = C.nx * C.ny * C.nz;
+    for (int t = threadIdx.x; t < m; t += blockDim.x)
+      down_node(F, C, t % C.nx, (t / C.nx) % C.ny, t / (C.nx * C.ny));
     __syncthreads();
   }
   {
     const MgLevel &B = T.lv[T.L];
-    for (int t = threadIdx.x; t < B.nx * B.ny; t += blockDim.x)
-      B.y[t] = B.g[t] * B.ia[t];
+    const int m = B.nx * B.ny * B.nz;
+    for (int t = threadIdx.x; t < m; t += blockDim.x) B.y[t] = B.g[t] * B.ia[t];
     __syncthreads();
   }
   for (int l = T.L - 1; l >= T.s; --l) {
     const MgLevel &F = T.lv[l], &C = T.lv[l + 1];
-    for (int t = threadIdx.x; t < F.nx * F.ny; t += blockDim.x) up_node(F, C, t % F.nx, t / F.nx);
+    const int m = F.nx * F.ny * F.nz;
+    for (int t = threadIdx.x; t < m; t += blockDim.x)
+      up_node(F, C, t % F.nx, (t / F.nx) % F.ny, t / (F.nx * F.ny));
     __syncthreads();
   }
 }
@@ -442,26 +483,27 @@ __device__ __forceinline__ bool last_block_2d(unsigned int *ticket, int *sh_flag
 __global__ void __launch_bounds__(kThreads)
 k_mg_up0(Grid g, CellGrid cg, int px, const float *__restrict__ s32, const int *__restrict__ kx,
          const float *__restrict__ w, const float *__restrict__ r, MgLevel L1,
-         float *__restrict__ z, MgCtl *ctl, double *part) {
+         float *__restrict__ zv, MgCtl *ctl, double *part) {
   __shared__ double sh[32];
   __shared__ int flag;
   if (ctl->done) return;
   const int kmin = ctl->kmin;
   float rz = 0.f;
-  auto u = [&](int64_t j, int xj, int yj) {
-    return fmaf(w[j], L1.y[(int64_t)(yj >> 1) * L1.nx + (xj >> 1)], kOmega * r[j]);
+  auto u = [&](int64_t j, int xj, int yj, int zj) {
+    return fmaf(w[j], L1.y[(xj >> 1) + (int64_t)L1.nx * ((yj >> 1) + (int64_t)L1.ny * (zj >> 1))],
+                kOmega * r[j]);
   };
-  MG_ROWS(g.ny) MG_COLS(g.nx) {
-    const int64_t i = (int64_t)y * px + x;
+  MG_ROWS(g.ny, g.nz) MG_COLS(g.nx) {
+    const int64_t i = x + (int64_t)px * rr;
     if (s32[i] == 0.f) {
-      z[i] = 0.f;
+      zv[i] = 0.f;
       continue;
     }
-    const int ki = kx_at(cg, x, y, kx);
-    const float ui = u(i, x, y);
-    const float Au = ui - nb0(g, cg, px, s32, kx, x, y, ki, u);
+    const int ki = kx_at(cg, x, y, z, kx);
+    const float ui = u(i, x, y, z);
+    const float Au = ui - nb0(g, cg, px, s32, kx, x, y, z, ki, u);
     const float zi = fmaf(kOmega, r[i] - Au, ui);
-    z[i] = zi;
+    zv[i] = zi;
     rz = fmaf(r[i] * zi, wdot(ki, kmin), rz);
   }
   const double bs = block_sum((double)rz, sh);
@@ -482,7 +524,7 @@ k_mg_up0(Grid g, CellGrid cg, int px, const float *__restrict__ s32, const int *
 // p = z + beta p_old, q = A p, <p, q>; alpha = rho / <p, q>.
 __global__ void __launch_bounds__(kThreads)
 k_mg_dir(Grid g, CellGrid cg, int px, const float *__restrict__ s32, const int *__restrict__ kx,
-         const float *__restrict__ z, const float *__restrict__ p_old, float *__restrict__ p_new,
+         const float *__restrict__ zv, const float *__restrict__ p_old, float *__restrict__ p_new,
          float *__restrict__ q, MgCtl *ctl, double *part) {
   __shared__ double sh[32];
   __shared__ int flag;
@@ -491,14 +533,14 @@ k_mg_dir(Grid g, CellGrid cg, int px, const float *__restrict__ s32, const int *
   const float beta = (float)ctl->beta;
   const bool first = ctl->first != 0;
   float pq = 0.f;
-  auto pv = [&](int64_t j, int, int) { return first ? z[j] : fmaf(beta, p_old[j], z[j]); };
-  MG_ROWS(g.ny) MG_COLS(g.nx) {
-    const int64_t i = (int64_t)y * px + x;
-    const float pi = pv(i, x, y);
+  auto pv = [&](int64_t j, int, int, int) { return first ? zv[j] : fmaf(beta, p_old[j], zv[j]); };
+  MG_ROWS(g.ny, g.nz) MG_COLS(g.nx) {
+    const int64_t i = x + (int64_t)px * rr;
+    const float pi = pv(i, x, y, z);
     float qi = 0.f;
     if (s32[i] != 0.f) {
-      const int ki = kx_at(cg, x, y, kx);
-      qi = pi - nb0(g, cg, px, s32, kx, x, y, ki, pv);
+      const int ki = kx_at(cg, x, y, z, kx);
+      qi = pi - nb0(g, cg, px, s32, kx, x, y, z, ki, pv);
       pq = fmaf(pi * qi, wdot(ki, kmin), pq);
     }
     p_new[i] = pi;
@@ -533,8 +575,8 @@ k_mg_step(Grid g, int px, const float *__restrict__ p, const float *__restrict__
   const int mode = ctl->mode;
   const float theta = ctl->theta;
   float rmax = 0.f, viol = 0.f;
-  MG_ROWS(g.ny) MG_COLS(g.nx) {
-    const int64_t i = (int64_t)y * px + x;
+  for (int rr = blockIdx.y; rr < g.ny * g.nz; rr += gridDim.y) MG_COLS(g.nx) {
+    const int64_t i = x + (int64_t)px * rr;
     const float di = fmaf(alpha, p[i], d[i]);
     const float ri = fmaf(-alpha, q[i], r[i]);
     d[i] = di;
@@ -631,37 +673,34 @@ void mg_destroy(MgState *mg) {
 eik_status mg_create(MgState **out, const Grid &g, const CellGrid &cg, int px, int num_sms,
                      cudaStream_t s) {
   *out = nullptr;
-  if (g.ndim != 2) {
-    g_msg = "the multigrid inner solve is two-dimensional";
-    return EIK_ERR_ARG;
-  }
   MgState *mg = new MgState();
   mg->g = g;
   mg->cg = cg;
   mg->px = px;
   mg->cap = num_sms * 8;
-  const int64_t n = (int64_t)g.nx * g.ny;
-  mg->nblk = (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, mg->cap));
   MgLevel L0;
   L0.nx = g.nx;
   L0.ny = g.ny;
+  L0.nz = g.nz;
   mg->lv.push_back(L0);
   bool ok = true;
-  int nx = g.nx, ny = g.ny;
-  while (ok && (nx > 1 || ny > 1) && (int)mg->lv.size() < kMaxLevels) {
+  int nx = g.nx, ny = g.ny, nz = g.nz;
+  while (ok && (nx > 1 || ny > 1 || nz > 1) && (int)mg->lv.size() < kMaxLevels) {
     nx = (nx + 1) / 2;
     ny = (ny + 1) / 2;
+    nz = (nz + 1) / 2;
     MgLevel L;
     L.nx = nx;
     L.ny = ny;
-    const size_t m = (size_t)nx * ny;
+    L.nz = nz;
+    const size_t m = (size_t)nx * ny * nz;
     ok = cudaMalloc(&L.a, 4 * m) == cudaSuccess && cudaMalloc(&L.ia, 4 * m) == cudaSuccess &&
-         cudaMalloc(&L.c, 16 * m) == cudaSuccess &&
+         cudaMalloc(&L.c, 4 * kDirs * m) == cudaSuccess &&
          cudaMalloc(&L.k, 4 * m) == cudaSuccess && cudaMalloc(&L.g, 4 * m) == cudaSuccess &&
          cudaMalloc(&L.y, 4 * m) == cudaSuccess;
     mg->lv.push_back(L);
   }
-  const size_t np = (size_t)g.ny * px;
+  const size_t np = (size_t)g.ny * g.nz * px;
   ok = ok && cudaMalloc(&mg->w, 4 * np) == cudaSuccess && cudaMalloc(&mg->z, 4 * np) == cudaSuccess &&
        cudaMalloc(&mg->p[0], 4 * np) == cudaSuccess && cudaMalloc(&mg->p[1], 4 * np) == cudaSuccess &&
        cudaMalloc(&mg->q, 4 * np) == cudaSuccess &&
@@ -685,28 +724,27 @@ eik_status mg_create(MgState **out, const Grid &g, const CellGrid &cg, int px, i
   return EIK_OK;
 }
 
-static int blocks_for(const MgState *mg, int64_t n) {
-  return (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, mg->cap));
-}
-
 // Row-strided launch grid of a level: columns by blockIdx.x, rows by
 // blockIdx.y, at most cap blocks.
-static dim3 grid2(const MgState *mg, int nx, int ny) {
+static dim3 grid2(const MgState *mg, int nx, int64_t rows) {
   const int gx = std::max(1, std::min((nx + kThreads - 1) / kThreads, mg->cap));
-  const int gy = std::max(1, std::min(ny, mg->cap / gx));
+  const int gy = (int)std::max<int64_t>(1, std::min<int64_t>(rows, mg->cap / gx));
   return dim3((unsigned)gx, (unsigned)gy, 1);
+}
+static dim3 grid_of(const MgState *mg, const MgLevel &L) {
+  return grid2(mg, L.nx, (int64_t)L.ny * L.nz);
 }
 
 eik_status mg_setup(MgState *mg, const MgFine &f, int kmin, cudaStream_t s) {
   const Grid &g = mg->g;
-  k_mg_weights<<<mg->nblk, kThreads, 0, s>>>(g, mg->cg, mg->px, f.s32, f.kx, f.St, mg->w);
+  k_mg_weights<<<grid_of(mg, mg->lv[0]), kThreads, 0, s>>>(g, mg->cg, mg->px, f.s32, f.kx, f.St,
+                                                            mg->w);
   MgLevel &L1 = mg->lv[1];
-  k_mg_coarsen0<<<blocks_for(mg, (int64_t)L1.nx * L1.ny), kThreads, 0, s>>>(
-      g, mg->cg, mg->px, f.s32, f.kx, mg->w, L1);
+  k_mg_coarsen0<<<grid_of(mg, L1), kThreads, 0, s>>>(g, mg->cg, mg->px, f.s32, f.kx, mg->w, L1);
   mg->launches += 2;
   for (size_t l = 1; l + 1 < mg->lv.size(); ++l) {
     MgLevel &C = mg->lv[l + 1];
-    k_mg_coarsen<<<blocks_for(mg, (int64_t)C.nx * C.ny), kThreads, 0, s>>>(mg->lv[l], C);
+    k_mg_coarsen<<<grid_of(mg, C), kThreads, 0, s>>>(mg->lv[l], C);
     mg->launches++;
   }
   GCK(cudaGetLastError());
@@ -719,29 +757,29 @@ eik_status mg_setup(MgState *mg, const MgFine &f, int kmin, cudaStream_t s) {
 // nodes, level 1 at the earliest.
 static int tail_start(const MgState *mg) {
   int l = 1;
-  while (l < (int)mg->lv.size() - 1 && (int64_t)mg->lv[l].nx * mg->lv[l].ny > kTailNodes) ++l;
+  while (l < (int)mg->lv.size() - 1 &&
+         (int64_t)mg->lv[l].nx * mg->lv[l].ny * mg->lv[l].nz > kTailNodes)
+    ++l;
   return l;
 }
 
 static void launch_iter(MgState *mg, const MgFine &f, int set, cudaStream_t s) {
   const Grid &g = mg->g;
   const int L = (int)mg->lv.size() - 1;   // coarsest level index
-  const dim3 g0 = grid2(mg, g.nx, g.ny);
-  k_mg_down0<<<grid2(mg, mg->lv[1].nx, mg->lv[1].ny), kThreads, 0, s>>>(
+  const dim3 g0 = grid_of(mg, mg->lv[0]);
+  k_mg_down0<<<grid_of(mg, mg->lv[1]), kThreads, 0, s>>>(
       g, mg->cg, mg->px, f.s32, f.kx, mg->w, f.r, mg->lv[1], mg->ctl);
   // levels 1 .. ts - 1 one launch each way; ts .. L in the single-block tail
   const int ts = tail_start(mg);
   for (int l = 1; l < ts; ++l)
-    k_mg_down<<<grid2(mg, mg->lv[l + 1].nx, mg->lv[l + 1].ny), kThreads, 0, s>>>(
-        mg->lv[l], mg->lv[l + 1], mg->ctl);
+    k_mg_down<<<grid_of(mg, mg->lv[l + 1]), kThreads, 0, s>>>(mg->lv[l], mg->lv[l + 1], mg->ctl);
   MgTail T{};
   for (int l = ts; l <= L; ++l) T.lv[l] = mg->lv[l];
   T.s = ts;
   T.L = L;
   k_mg_tail<<<1, kTailThreads, 0, s>>>(T, mg->ctl);
   for (int l = ts - 1; l >= 1; --l)
-    k_mg_up<<<grid2(mg, mg->lv[l].nx, mg->lv[l].ny), kThreads, 0, s>>>(mg->lv[l], mg->lv[l + 1],
-                                                                         mg->ctl);
+    k_mg_up<<<grid_of(mg, mg->lv[l]), kThreads, 0, s>>>(mg->lv[l], mg->lv[l + 1], mg->ctl);
   k_mg_up0<<<g0, kThreads, 0, s>>>(g, mg->cg, mg->px, f.s32, f.kx, mg->w, f.r, mg->lv[1], mg->z,
                                    mg->ctl, mg->part);
   k_mg_dir<<<g0, kThreads, 0, s>>>(g, mg->cg, mg->px, f.s32, f.kx, mg->z, mg->p[set],

@@ -29,7 +29,7 @@ struct MixedArgs {
   eik_options opt;
 };
 
-// precond: EIK_PRECOND_* of the inner solve (multigrid: 2D only).
+// precond: EIK_PRECOND_* of the inner solve.
 eik_status mixed_create(MixedState **out, const Grid &g, const TileCount &tc, int num_sms,
                         int tile_override, int precond, cudaStream_t s);
 // A member of a packed 2D batch: its FP32 inner-CG arrays and control block

@@ -92,13 +92,13 @@ def test_null_arguments_rejected_without_gpu(lib):
 
 
 def test_preconditioner_option_checked_without_gpu(lib):
-    """An unknown precond, multigrid in FP64 and multigrid on a 3D grid are
-    rejected before any CUDA call."""
+    """An unknown precond and multigrid in FP64 are rejected before any CUDA
+    call."""
     from paper_1403_1937_gb300 import _lib
     P = ctypes.c_void_p(0x1000)      # never dereferenced: the checks fail first
     for ndim, prec, pc in ((2, _lib.PREC_MIXED, 2), (2, _lib.PREC_MIXED, -1),
                            (2, _lib.PREC_FP64, _lib.PRECOND_MULTIGRID),
-                           (3, _lib.PREC_MIXED, _lib.PRECOND_MULTIGRID)):
+                           (3, _lib.PREC_FP64, _lib.PRECOND_MULTIGRID)):
         o = _lib.default_options()
         o.precision = prec
         o.precond = pc

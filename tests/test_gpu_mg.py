@@ -159,10 +159,9 @@ def test_option_checks(eik):
     import torch
     inst3 = wl.config3(n=8)
     f = torch.from_numpy(inst3.f).cuda()
-    for prec in ("mixed", "fp64"):
-        opt = eik.make_options(precision=prec, precond="multigrid")
-        with pytest.raises(_lib.EikError):
-            eik.eik_create(inst3.dims, inst3.h, inst3.hbar, f, inst3.src_idx, None, opt)
+    opt = eik.make_options(precision="fp64", precond="multigrid")
+    with pytest.raises(_lib.EikError):
+        eik.eik_create(inst3.dims, inst3.h, inst3.hbar, f, inst3.src_idx, None, opt)
     inst = wl.config1()
     opt = eik.make_options(precision="fp64", precond="multigrid")
     with pytest.raises(_lib.EikError):
@@ -186,6 +185,68 @@ def test_batch_of_multigrid_instances(eik):
         off += inst.n
         S_ref, _, _ = fd.solve(inst.f, inst.dims, inst.h, inst.hbar, inst.src_idx, inst.src_U)
         assert np.max(np.abs(S - S_ref)) <= S_ABS
+
+
+@pytest.mark.parametrize("seed,boundary,with_U", [
+    (2, "half_cell", False), (3, "half_cell", True), (5, "drop_edge", False),
+])
+def test_random_ragged_3d_multigrid(eik, seed, boundary, with_U):
+    """3D: random sides (odd and even: boxes of 1 to 8 nodes on every level),
+    sources on faces and corners, source values U."""
+    inst = wl.random_small(600 + seed, ndim=3, max_side=40, min_side=3, nsrc_max=6,
+                           with_U=with_U, hbar_over_h=(1.0, 6.0))
+    S, _, _ = solve(eik, inst, boundary=boundary)
+    S_ref, _, sys = fd.solve(inst.f, inst.dims, inst.h, inst.hbar, inst.src_idx, inst.src_U,
+                             boundary=1 if boundary == "drop_edge" else 0)
+    assert np.max(np.abs(S - S_ref)) <= S_ABS
+    assert np.array_equal(S[sys.src], sys.U)
+
+
+def test_c3_reduced_multigrid_iterations(eik):
+    """Config-3 structure at 64^3: the S bound against the oracle, and fewer
+    inner iterations than the Jacobi-preconditioned inner CG."""
+    inst = wl.config3(n=64)
+    S, st_mg, _ = solve(eik, inst, tol=1e-8)
+    S_ref, _, _ = fd.solve(inst.f, inst.dims, inst.h, inst.hbar, inst.src_idx)
+    assert np.max(np.abs(S - S_ref)) <= S_ABS
+    _, st_j, _ = solve(eik, inst, tol=1e-8, precond="jacobi")
+    print(f"\n64^3 inner iterations: multigrid {st_mg['inner_iters']} "
+          f"({st_mg['outer_iters']} steps), Jacobi {st_j['inner_iters']} "
+          f"({st_j['outer_iters']} steps)")
+    assert 2 * st_mg["inner_iters"] <= st_j["inner_iters"]
+
+
+@pytest.mark.parametrize("dims,src", [
+    ((2, 2, 2), [7]),
+    ((33, 2, 2), [0, 33, 66, 99]),
+    ((3, 5, 2), [0, 29]),
+    ((2, 2, 3), [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11]),   # every node a source
+])
+def test_edge_cases_3d_multigrid(eik, dims, src):
+    n = int(np.prod(dims))
+    inst = wl.Instance(dims, 1.0 / (max(dims) - 1), 0.3 / (max(dims) - 1) * 4,
+                       np.random.default_rng(n).uniform(0.5, 2.0, dims[::-1]),
+                       np.array(src, dtype=np.int64), np.zeros(len(src)))
+    S, _, _ = solve(eik, inst)
+    if len(set(src)) == n:
+        assert np.all(S == 0.0)
+        return
+    S_ref, _, sys = fd.solve(inst.f, inst.dims, inst.h, inst.hbar, inst.src_idx)
+    assert np.max(np.abs(S - S_ref)) <= S_ABS
+    assert np.array_equal(S[sys.src], sys.U)
+
+
+@pytest.mark.slow
+def test_c3_full_size_multigrid(eik):
+    """Config 3 at 256^3 in the bench's multigrid configuration (tol 1e-7)."""
+    inst = wl.config3()
+    S, stats, _ = solve(eik, inst, tol=1e-7)
+    S_ref, _, _, info = cg.solve(inst.f, inst.dims, inst.h, inst.hbar, inst.src_idx,
+                                 tol=1e-13)
+    assert info["status"] == 0
+    print(f"\n256^3 multigrid: {stats['inner_iters']} inner iterations, "
+          f"{stats['outer_iters']} steps, {stats['ms']:.1f} ms")
+    assert np.max(np.abs(S - S_ref)) <= S_ABS
 
 
 @pytest.mark.slow
