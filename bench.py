@@ -622,7 +622,7 @@ def run_batch(args, emit=True):
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1e3 * total / args.steps, 3), "higher_is_better": True,
             "scaling": "strong", "vs_baseline": None,
-            "dtype": "f64" if head_mode == "fp64" else "f32+f64", "data": "synthetic",
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
             "config": {"workload": f"batched 2D: {len(all_insts)} instances, sides 64..1024, "
                                    "Fourier f in [0.5,1.5], 1-8 sources, hbar in {2h,4h,8h}",
                        "instances": len(all_insts), "instances_rank0": len(insts),
