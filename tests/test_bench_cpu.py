@@ -36,6 +36,25 @@ def test_roofline_mixed_is_hbm_bound():
     assert r["share_of_kernel_time"] == pytest.approx(0.4 / 1.1, abs=1e-3)
 
 
+@pytest.mark.parametrize("dims,bytes_per_node", [((2048, 2048), 95), ((256, 256, 256), 85)])
+def test_multigrid_iteration_roofline_is_separate(dims, bytes_per_node):
+    """The multigrid-preconditioned iteration (all its kernels, timed as one
+    unit) never becomes the dominant kernel of a Jacobi line; asked for by
+    name it reports its own per-dimension algorithmic bytes."""
+    import bench
+    inst = _Inst(dims)
+    res = {"kernel_ms": {"mixed_mg": (0.3, 90, 27.0), "mixed_cg": (0.04, 10, 0.4),
+                         "mixed_residual64": (0.4, 1, 0.4)}}
+    r = bench.roofline(res, inst, "c2")
+    assert r["kernel"] == "mixed_cg"
+    m = bench.roofline(res, inst, "c2", only="mixed_mg")
+    assert m["kernel"] == "mixed_mg" and m["bound"] == "hbm"
+    assert m["algorithmic_bytes_per_launch"] == bytes_per_node * inst.n
+    assert m["achieved"] == pytest.approx(bytes_per_node * inst.n / 0.3e-3 / 1e9, rel=1e-3)
+    assert bench.algo_bytes("mixed_mg", inst) == bytes_per_node
+    assert bench.algo_bytes("mixed_cg", inst) == 28
+
+
 @pytest.mark.parametrize("dims,flops", [((2048, 2048), 10), ((64, 64, 64), 12)])
 def test_roofline_fp64_is_bound_by_the_fp64_rate(dims, flops):
     import bench
