@@ -10,7 +10,10 @@ componentwise tolerance, restarts, log epilogue).
 
 Metric: stencil-PCG GLUPS = sum over steps of (unknowns x CG iterations) /
 device seconds / 1e9, plus time-to-solution per step.  Both precision modes
-are timed; the headline line reports the mode given by --precision.
+are timed; the headline line reports the mode given by --precision.  The
+mixed solve with the multigrid-preconditioned inner solve (componentwise tol
+--mg-tol) is timed beside them and compared by time to solution
+(--no-mg skips it; --modes mg times only it).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """

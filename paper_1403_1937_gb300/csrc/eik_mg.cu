@@ -300,7 +300,6 @@ __device__ __forceinline__ int box_k(const MgLevel &F, int X, int Y, int Z) {
 __global__ void k_mg_coarsen(MgLevel F, MgLevel C) {
   const int64_t m = (int64_t)C.nx * C.ny * C.nz;
   const int64_t mf = (int64_t)F.nx * F.ny * F.nz;
-  const int64_t plf = (int64_t)F.nx * F.ny;
   MG_ROWS(C.ny, C.nz) MG_COLS(C.nx) {
     const int64_t t = x + (int64_t)C.nx * rr;
     const int kc = box_k(F, x, y, z);
@@ -336,7 +335,6 @@ __global__ void k_mg_coarsen(MgLevel F, MgLevel C) {
           add(c + 1 < F.nz, c + 1 <= z1, kT);
           A += r * row;
         }
-    (void)plf;
     C.a[t] = (float)A;
     C.ia[t] = (float)(1.0 / A);
     C.c[kW * m + t] = (x > 0) ? (float)cd[kW] : 0.f;
@@ -612,7 +610,7 @@ k_mg_step(Grid g, int px, const float *__restrict__ p, const float *__restrict__
 struct MgState {
   Grid g;
   CellGrid cg;
-  int px = 0, nblk = 0, cap = 0;
+  int px = 0, cap = 0;
   std::vector<MgLevel> lv;   // lv[0]: level-0 sizes only
   float *w = nullptr, *z = nullptr, *p[2] = {nullptr, nullptr}, *q = nullptr;
   MgCtl *ctl = nullptr, *h_ctl = nullptr;
