@@ -118,15 +118,23 @@ __device__ __forceinline__ float p2f(int e) {
 // index j.  The exponent is looked up only where the neighbour lies in
 // another cell.  Edge weights: the product of the face factors of the other
 // axes (Sec. 6 with zero-flux faces, half cells on the faces).
-template <class V>
+// Linear index of (x, y, z) on a level of pitch nx and ny rows per plane
+// (DIM = 2: z is 0).
+template <int DIM>
+__device__ __forceinline__ int64_t lin(int x, int y, int z, int nx, int ny) {
+  if constexpr (DIM == 3) return x + (int64_t)nx * (y + (int64_t)ny * z);
+  else return x + (int64_t)nx * y;
+}
+
+template <int DIM, class V>
 __device__ __forceinline__ float nb0(const Grid &g, const CellGrid &cg, int px,
                                      const float *__restrict__ s32, const int *__restrict__ kx,
                                      int x, int y, int z, int ki, V v) {
   float acc = 0.f;
   const int mask = cg.B - 1;
-  const float hx = face(x, g.nx, g.boundary), hy = face(y, g.ny, g.boundary), hz = facez(g, z);
-  const int64_t pz = (int64_t)px * g.ny;
-  const int64_t i = x + (int64_t)px * (y + (int64_t)g.ny * z);
+  const float hx = face(x, g.nx, g.boundary), hy = face(y, g.ny, g.boundary);
+  const float hz = (DIM == 3) ? facez(g, z) : 1.f;
+  const int64_t i = lin<DIM>(x, y, z, px, g.ny);
   if (x > 0) {
     const float f = ((x & mask) == 0) ? p2f(ki - kx_at(cg, x - 1, y, z, kx)) : 1.f;
     acc = fmaf(hy * hz * s32[i - 1] * f, v(i - 1, x - 1, y, z), acc);
@@ -143,31 +151,36 @@ __device__ __forceinline__ float nb0(const Grid &g, const CellGrid &cg, int px,
     const float f = (((y + 1) & mask) == 0) ? p2f(ki - kx_at(cg, x, y + 1, z, kx)) : 1.f;
     acc = fmaf(hx * hz * s32[i + px] * f, v(i + px, x, y + 1, z), acc);
   }
-  if (z > 0) {
-    const float f = ((z & mask) == 0) ? p2f(ki - kx_at(cg, x, y, z - 1, kx)) : 1.f;
-    acc = fmaf(hx * hy * s32[i - pz] * f, v(i - pz, x, y, z - 1), acc);
-  }
-  if (z + 1 < g.nz) {
-    const float f = (((z + 1) & mask) == 0) ? p2f(ki - kx_at(cg, x, y, z + 1, kx)) : 1.f;
-    acc = fmaf(hx * hy * s32[i + pz] * f, v(i + pz, x, y, z + 1), acc);
+  if constexpr (DIM == 3) {
+    const int64_t pz = (int64_t)px * g.ny;
+    if (z > 0) {
+      const float f = ((z & mask) == 0) ? p2f(ki - kx_at(cg, x, y, z - 1, kx)) : 1.f;
+      acc = fmaf(hx * hy * s32[i - pz] * f, v(i - pz, x, y, z - 1), acc);
+    }
+    if (z + 1 < g.nz) {
+      const float f = (((z + 1) & mask) == 0) ? p2f(ki - kx_at(cg, x, y, z + 1, kx)) : 1.f;
+      acc = fmaf(hx * hy * s32[i + pz] * f, v(i + pz, x, y, z + 1), acc);
+    }
   }
   return s32[i] * acc;
 }
 
 // Coarse-level operator (A u)_t for node (x, y, z) of a level; u(j, xj, yj,
 // zj) by dense index and coordinates.
-template <class V>
+template <int DIM, class V>
 __device__ __forceinline__ float apply_l(const MgLevel &L, int x, int y, int z, V u) {
-  const int64_t m = (int64_t)L.nx * L.ny * L.nz;
   const int64_t pl = (int64_t)L.nx * L.ny;
-  const int64_t i = x + (int64_t)L.nx * (y + (int64_t)L.ny * z);
+  const int64_t m = (DIM == 3) ? pl * L.nz : pl;
+  const int64_t i = lin<DIM>(x, y, z, L.nx, L.ny);
   float acc = fabsf(L.a[i]) * u(i, x, y, z);
   if (x > 0) acc = fmaf(L.c[kW * m + i], u(i - 1, x - 1, y, z), acc);
   if (x + 1 < L.nx) acc = fmaf(L.c[kE * m + i], u(i + 1, x + 1, y, z), acc);
   if (y > 0) acc = fmaf(L.c[kS * m + i], u(i - L.nx, x, y - 1, z), acc);
   if (y + 1 < L.ny) acc = fmaf(L.c[kN * m + i], u(i + L.nx, x, y + 1, z), acc);
-  if (z > 0) acc = fmaf(L.c[kB * m + i], u(i - pl, x, y, z - 1), acc);
-  if (z + 1 < L.nz) acc = fmaf(L.c[kT * m + i], u(i + pl, x, y, z + 1), acc);
+  if constexpr (DIM == 3) {
+    if (z > 0) acc = fmaf(L.c[kB * m + i], u(i - pl, x, y, z - 1), acc);
+    if (z + 1 < L.nz) acc = fmaf(L.c[kT * m + i], u(i + pl, x, y, z + 1), acc);
+  }
   return acc;
 }
 
@@ -349,6 +362,7 @@ __global__ void k_mg_coarsen(MgLevel F, MgLevel C) {
 
 // ------------------------------------------------------------- V-cycle
 // Level 0 down: y = omega r, t = r - A y, g1 = sum over the box of w_i t_i.
+template <int DIM>
 __global__ void k_mg_down0(Grid g, CellGrid cg, int px, const float *__restrict__ s32,
                            const int *__restrict__ kx, const float *__restrict__ w,
                            const float *__restrict__ r, MgLevel L1, const MgCtl *ctl) {
@@ -356,14 +370,15 @@ __global__ void k_mg_down0(Grid g, CellGrid cg, int px, const float *__restrict_
   auto rv = [&](int64_t j, int, int, int) { return r[j]; };
   MG_ROWS(L1.ny, L1.nz) MG_COLS(L1.nx) {
     float sum = 0.f;
-    for (int cz = 2 * z; cz <= min(2 * z + 1, g.nz - 1); ++cz)
+    const int zt = (DIM == 3) ? min(2 * z + 1, g.nz - 1) : 0;
+    for (int cz = 2 * z; cz <= zt; ++cz)
       for (int cy = 2 * y; cy <= min(2 * y + 1, g.ny - 1); ++cy)
         for (int cx = 2 * x; cx <= min(2 * x + 1, g.nx - 1); ++cx) {
-          const int64_t i = cx + (int64_t)px * (cy + (int64_t)g.ny * cz);
+          const int64_t i = lin<DIM>(cx, cy, cz, px, g.ny);
           const float wi = w[i];
           if (wi == 0.f) continue;
           const int ki = kx_at(cg, cx, cy, cz, kx);
-          const float off = nb0(g, cg, px, s32, kx, cx, cy, cz, ki, rv);
+          const float off = nb0<DIM>(g, cg, px, s32, kx, cx, cy, cz, ki, rv);
           // (A (omega r))_i = omega (r_i - off)
           const float ti = r[i] - kOmega * (r[i] - off);
           sum = fmaf(wi, ti, sum);
@@ -374,50 +389,54 @@ __global__ void k_mg_down0(Grid g, CellGrid cg, int px, const float *__restrict_
 
 // Level l down (l >= 1) at coarse node (x, y, z): y = omega g / a on the
 // box, t = g - A y, restricted to level l + 1.
+template <int DIM>
 __device__ __forceinline__ void down_node(const MgLevel &F, const MgLevel &C, int x, int y, int z) {
   auto yv = [&](int64_t j, int, int, int) { return kOmega * F.g[j] * F.ia[j]; };
-  const int64_t t = x + (int64_t)C.nx * (y + (int64_t)C.ny * z);
+  const int64_t t = lin<DIM>(x, y, z, C.nx, C.ny);
   const int kc = C.k[t];
   float sum = 0.f;
   if (C.a[t] >= 0.f) {
-    for (int cz = 2 * z; cz <= min(2 * z + 1, F.nz - 1); ++cz)
+    const int zt = (DIM == 3) ? min(2 * z + 1, F.nz - 1) : 0;
+    for (int cz = 2 * z; cz <= zt; ++cz)
       for (int cy = 2 * y; cy <= min(2 * y + 1, F.ny - 1); ++cy)
         for (int cx = 2 * x; cx <= min(2 * x + 1, F.nx - 1); ++cx) {
-          const int64_t i = cx + (int64_t)F.nx * (cy + (int64_t)F.ny * cz);
+          const int64_t i = lin<DIM>(cx, cy, cz, F.nx, F.ny);
           if (F.a[i] < 0.f) continue;
-          const float ti = F.g[i] - apply_l(F, cx, cy, cz, yv);
+          const float ti = F.g[i] - apply_l<DIM>(F, cx, cy, cz, yv);
           sum = fmaf(p2f(2 * (kc - F.k[i])), ti, sum);
         }
   }
   C.g[t] = sum;
 }
 
+template <int DIM>
 __global__ void k_mg_down(MgLevel F, MgLevel C, const MgCtl *ctl) {
   if (ctl->done) return;
-  MG_ROWS(C.ny, C.nz) MG_COLS(C.nx) down_node(F, C, x, y, z);
+  MG_ROWS(C.ny, C.nz) MG_COLS(C.nx) down_node<DIM>(F, C, x, y, z);
 }
 
 // Level l up (l >= 1) at node (x, y, z): u = omega g / a + y(parent);
 // y = u + omega (g - A u) / a.
+template <int DIM>
 __device__ __forceinline__ void up_node(const MgLevel &F, const MgLevel &C, int x, int y, int z) {
-  const int64_t t = x + (int64_t)F.nx * (y + (int64_t)F.ny * z);
+  const int64_t t = lin<DIM>(x, y, z, F.nx, F.ny);
   if (F.a[t] < 0.f) {
     F.y[t] = 0.f;
     return;
   }
   auto uat = [&](int64_t j, int xj, int yj, int zj) {
-    const float par =
-        (F.a[j] >= 0.f) ? C.y[(xj >> 1) + (int64_t)C.nx * ((yj >> 1) + (int64_t)C.ny * (zj >> 1))] : 0.f;
+    const float par = (F.a[j] >= 0.f) ? C.y[lin<DIM>(xj >> 1, yj >> 1, zj >> 1, C.nx, C.ny)] : 0.f;
     return fmaf(kOmega * F.g[j], F.ia[j], par);
   };
   const float ut = uat(t, x, y, z);
-  const float Au = apply_l(F, x, y, z, uat);
+  const float Au = apply_l<DIM>(F, x, y, z, uat);
   F.y[t] = fmaf(kOmega * (F.g[t] - Au), F.ia[t], ut);
 }
 
+template <int DIM>
 __global__ void k_mg_up(MgLevel F, MgLevel C, const MgCtl *ctl) {
   if (ctl->done) return;
-  MG_ROWS(F.ny, F.nz) MG_COLS(F.nx) up_node(F, C, x, y, z);
+  MG_ROWS(F.ny, F.nz) MG_COLS(F.nx) up_node<DIM>(F, C, x, y, z);
 }
 
 // The small levels s .. L of the V-cycle in one block: down sweeps, the
@@ -429,13 +448,14 @@ struct MgTail {
   MgLevel lv[kMaxLevels];
   int s, L;
 };
+template <int DIM>
 __global__ void __launch_bounds__(kTailThreads) k_mg_tail(MgTail T, const MgCtl *ctl) {
   if (ctl->done) return;
   for (int l = T.s; l < T.L; ++l) {
     const MgLevel &F = T.lv[l], &C = T.lv[l + 1];
     const int m = C.nx * C.ny * C.nz;
     for (int t = threadIdx.x; t < m; t += blockDim.x)
-      down_node(F, C, t % C.nx, (t / C.nx) % C.ny, t / (C.nx * C.ny));
+      down_node<DIM>(F, C, t % C.nx, (t / C.nx) % C.ny, t / (C.nx * C.ny));
     __syncthreads();
   }
   {
@@ -448,7 +468,7 @@ __global__ void __launch_bounds__(kTailThreads) k_mg_tail(MgTail T, const MgCtl 
     const MgLevel &F = T.lv[l], &C = T.lv[l + 1];
     const int m = F.nx * F.ny * F.nz;
     for (int t = threadIdx.x; t < m; t += blockDim.x)
-      up_node(F, C, t % F.nx, (t / F.nx) % F.ny, t / (F.nx * F.ny));
+      up_node<DIM>(F, C, t % F.nx, (t / F.nx) % F.ny, t / (F.nx * F.ny));
     __syncthreads();
   }
 }
@@ -478,6 +498,7 @@ __device__ __forceinline__ bool last_block_2d(unsigned int *ticket, int *sh_flag
 }
 
 // Level 0 up: u = omega r + w y1(parent), z = u + omega (r - A u); rho = <r, z>.
+template <int DIM>
 __global__ void __launch_bounds__(kThreads)
 k_mg_up0(Grid g, CellGrid cg, int px, const float *__restrict__ s32, const int *__restrict__ kx,
          const float *__restrict__ w, const float *__restrict__ r, MgLevel L1,
@@ -488,8 +509,7 @@ k_mg_up0(Grid g, CellGrid cg, int px, const float *__restrict__ s32, const int *
   const int kmin = ctl->kmin;
   float rz = 0.f;
   auto u = [&](int64_t j, int xj, int yj, int zj) {
-    return fmaf(w[j], L1.y[(xj >> 1) + (int64_t)L1.nx * ((yj >> 1) + (int64_t)L1.ny * (zj >> 1))],
-                kOmega * r[j]);
+    return fmaf(w[j], L1.y[lin<DIM>(xj >> 1, yj >> 1, zj >> 1, L1.nx, L1.ny)], kOmega * r[j]);
   };
   MG_ROWS(g.ny, g.nz) MG_COLS(g.nx) {
     const int64_t i = x + (int64_t)px * rr;
@@ -499,7 +519,7 @@ k_mg_up0(Grid g, CellGrid cg, int px, const float *__restrict__ s32, const int *
     }
     const int ki = kx_at(cg, x, y, z, kx);
     const float ui = u(i, x, y, z);
-    const float Au = ui - nb0(g, cg, px, s32, kx, x, y, z, ki, u);
+    const float Au = ui - nb0<DIM>(g, cg, px, s32, kx, x, y, z, ki, u);
     const float zi = fmaf(kOmega, r[i] - Au, ui);
     zv[i] = zi;
     rz = fmaf(r[i] * zi, wdot(ki, kmin), rz);
@@ -520,6 +540,7 @@ k_mg_up0(Grid g, CellGrid cg, int px, const float *__restrict__ s32, const int *
 }
 
 // p = z + beta p_old, q = A p, <p, q>; alpha = rho / <p, q>.
+template <int DIM>
 __global__ void __launch_bounds__(kThreads)
 k_mg_dir(Grid g, CellGrid cg, int px, const float *__restrict__ s32, const int *__restrict__ kx,
          const float *__restrict__ zv, const float *__restrict__ p_old, float *__restrict__ p_new,
@@ -538,7 +559,7 @@ k_mg_dir(Grid g, CellGrid cg, int px, const float *__restrict__ s32, const int *
     float qi = 0.f;
     if (s32[i] != 0.f) {
       const int ki = kx_at(cg, x, y, z, kx);
-      qi = pi - nb0(g, cg, px, s32, kx, x, y, z, ki, pv);
+      qi = pi - nb0<DIM>(g, cg, px, s32, kx, x, y, z, ki, pv);
       pq = fmaf(pi * qi, wdot(ki, kmin), pq);
     }
     p_new[i] = pi;
@@ -761,29 +782,39 @@ static int tail_start(const MgState *mg) {
   return l;
 }
 
-static void launch_iter(MgState *mg, const MgFine &f, int set, cudaStream_t s) {
+template <int DIM>
+static void launch_iter_d(MgState *mg, const MgFine &f, int set, cudaStream_t s) {
   const Grid &g = mg->g;
   const int L = (int)mg->lv.size() - 1;   // coarsest level index
   const dim3 g0 = grid_of(mg, mg->lv[0]);
-  k_mg_down0<<<grid_of(mg, mg->lv[1]), kThreads, 0, s>>>(
+  k_mg_down0<DIM><<<grid_of(mg, mg->lv[1]), kThreads, 0, s>>>(
       g, mg->cg, mg->px, f.s32, f.kx, mg->w, f.r, mg->lv[1], mg->ctl);
   // levels 1 .. ts - 1 one launch each way; ts .. L in the single-block tail
   const int ts = tail_start(mg);
   for (int l = 1; l < ts; ++l)
-    k_mg_down<<<grid_of(mg, mg->lv[l + 1]), kThreads, 0, s>>>(mg->lv[l], mg->lv[l + 1], mg->ctl);
+    k_mg_down<DIM><<<grid_of(mg, mg->lv[l + 1]), kThreads, 0, s>>>(mg->lv[l], mg->lv[l + 1],
+                                                                     mg->ctl);
   MgTail T{};
   for (int l = ts; l <= L; ++l) T.lv[l] = mg->lv[l];
   T.s = ts;
   T.L = L;
-  k_mg_tail<<<1, kTailThreads, 0, s>>>(T, mg->ctl);
+  k_mg_tail<DIM><<<1, kTailThreads, 0, s>>>(T, mg->ctl);
   for (int l = ts - 1; l >= 1; --l)
-    k_mg_up<<<grid_of(mg, mg->lv[l]), kThreads, 0, s>>>(mg->lv[l], mg->lv[l + 1], mg->ctl);
-  k_mg_up0<<<g0, kThreads, 0, s>>>(g, mg->cg, mg->px, f.s32, f.kx, mg->w, f.r, mg->lv[1], mg->z,
+    k_mg_up<DIM><<<grid_of(mg, mg->lv[l]), kThreads, 0, s>>>(mg->lv[l], mg->lv[l + 1], mg->ctl);
+  k_mg_up0<DIM><<<g0, kThreads, 0, s>>>(g, mg->cg, mg->px, f.s32, f.kx, mg->w, f.r, mg->lv[1], mg->z,
                                    mg->ctl, mg->part);
-  k_mg_dir<<<g0, kThreads, 0, s>>>(g, mg->cg, mg->px, f.s32, f.kx, mg->z, mg->p[set],
+  k_mg_dir<DIM><<<g0, kThreads, 0, s>>>(g, mg->cg, mg->px, f.s32, f.kx, mg->z, mg->p[set],
                                    mg->p[1 - set], mg->q, mg->ctl, mg->part);
   k_mg_step<<<g0, kThreads, 0, s>>>(g, mg->px, mg->p[1 - set], mg->q, f.xref, f.d, f.r, mg->ctl,
                                     mg->part, mg->cap);
+}
+
+// One PCG iteration with the kernels specialised to the grid's dimension.
+static void launch_iter(MgState *mg, const MgFine &f, int set, cudaStream_t s) {
+  if (mg->g.ndim == 3)
+    launch_iter_d<3>(mg, f, set, s);
+  else
+    launch_iter_d<2>(mg, f, set, s);
 }
 
 static int launches_per_iter(const MgState *mg) { return 2 * (tail_start(mg) - 1) + 5; }
